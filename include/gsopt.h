@@ -1,0 +1,276 @@
+/*
+ * gsopt.h — C ABI of libgsopt.so, the GB300 (sm_103a) AdamW-GS optimizer step
+ * of "A Step to Decouple Optimization in 3DGS" (arXiv 2601.16736).
+ *
+ * The library updates the attributes of N Gaussian primitives in place with
+ * the paper's recomposed optimizer: Sparse Adam over the primitives visible
+ * from the current view (Sec. 3.1, Eq. meth::sparse_beta), Decoupled
+ * Attribute Regularization on opacity and scale (Sec. 3.3,
+ * Eq. disentangled_adam; App. Eqs. disentangled_opacity / _scaling),
+ * Re-State Regularization of StSS-sampled primitives (Sec. 3.2,
+ * Eq. meth::restate), and it keeps its per-primitive optimizer state
+ * consistent when the primitive set changes (Sec. 2: densification, pruning,
+ * MCMC relocation; App. "Scaling in RSR" item 1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every call returns a gs_status.  Arguments are validated on the host
+ *   before anything is launched; an invalid argument returns
+ *   GS_ERR_INVALID_ARG and launches nothing.  Device pointers are checked to
+ *   be device allocations that hold the stated number of bytes (driver
+ *   address-range query, cached per pointer).
+ * - "device" pointers are CUDA global memory on the context's device,
+ *   owned by the caller unless stated otherwise; "host" pointers are host
+ *   memory (pinned memory gives asynchronous copies).
+ * - Work is enqueued on `stream` (a cudaStream_t; NULL = the legacy default
+ *   stream) and is asynchronous unless stated otherwise.  A CUDA error during
+ *   a call returns GS_ERR_CUDA and latches the context: later calls return
+ *   GS_ERR_STATE until it is destroyed.
+ * - A context is not thread-safe; calls on one context must be ordered on
+ *   one stream (or externally synchronised).
+ * - Primitive attributes use a structure-of-arrays layout, one float32
+ *   array per group, row-major within the group:
+ *       xyz [N][3]  position mu
+ *       scale [N][3]  log-scale kappa (s = exp(kappa))
+ *       rot [N][4]  quaternion
+ *       opacity [N][1]  opacity logit tau (o = sigmoid(tau))
+ *       sh [N][48]  16 SH coefficients x RGB; columns 0-2 are the DC term
+ *   59 values per primitive.  rot and sh must be 16-byte aligned, the others
+ *   4-byte aligned.  The canonical 59-column row used by the state
+ *   export/import concatenates the groups in that order.
+ * - N (the row count) must be below 2^31 - 1.
+ */
+#ifndef GSOPT_H
+#define GSOPT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GS_ABI_VERSION 1
+#define GS_NUM_COLS 59
+
+typedef enum gs_status {
+    GS_OK = 0,
+    GS_ERR_INVALID_ARG = 1, /* bad pointer, size, alignment or value; nothing launched */
+    GS_ERR_CUDA = 2,        /* a CUDA runtime/driver call failed; context latched   */
+    GS_ERR_OOM = 3,         /* device allocation failed                               */
+    GS_ERR_UNSUPPORTED = 4, /* valid request this build does not implement            */
+    GS_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up                     */
+    GS_ERR_STATE = 6        /* context latched by an earlier error                    */
+} gs_status;
+
+/* Storage of the Adam moments m, v (arithmetic is FP32 in every case). */
+typedef enum gs_moment_prec {
+    GS_MOM_FP32 = 0,
+    GS_MOM_BF16 = 1,
+    GS_MOM_FP8E4M3 = 2 /* e4m3 codes with FP32 scales per (256-row block, column) */
+} gs_moment_prec;
+
+/* Regulariser form.  GS_REG_DAR is the paper's AdamW-GS (Eq. disentangled_adam);
+ * the others are the ablations of App. "AdamW Style Decoupling" and
+ * Sec. 3.2 (Eqs. disentangled_adam2, disentangled_adamwithcliping,
+ * meth::undisentangled_mom). */
+typedef enum gs_reg_mode {
+    GS_REG_DAR = 0,
+    GS_REG_COUPLED = 1,
+    GS_REG_ADAMW = 2,
+    GS_REG_ADAMW_CLIP = 3
+} gs_reg_mode;
+
+typedef struct gs_attrs {        /* device, caller-owned, updated in place */
+    float *xyz, *scale, *rot, *opacity, *sh;
+} gs_attrs;
+
+typedef struct gs_grads {        /* device (host for gs_step_host), read-only */
+    const float *xyz, *scale, *rot, *opacity, *sh;
+} gs_grads;
+
+/* Static configuration (paper defaults in brackets, App. "Hyperparameter
+ * Selection"). */
+typedef struct gs_opt_config {
+    double beta1, beta2;     /* Adam decay rates [0.9, 0.999]; 0 <= beta < 1          */
+    float eps;               /* added outside the square root, Eq. meth::adam_update   */
+    float lambda_o;          /* DAR weight on opacity [1e-3]                            */
+    float lambda_s;          /* DAR weight on scale [1e-5]                              */
+    float clip_o, clip_s;    /* C_t [10, 10]                                            */
+    float alpha1, alpha2;    /* RSR factors [0.2, 0.04]; 0 <= alpha < 1                 */
+    int32_t prec;            /* gs_moment_prec                                          */
+    int32_t bias_mode;       /* 0: per-primitive step count t (Sec. 3.2), 1: global k  */
+    int32_t reg_mode;        /* gs_reg_mode                                             */
+    int32_t reserved;        /* must be 0                                               */
+    int64_t n_pixels;        /* training-image pixel count; the DAR normaliser N_I is
+                                derived from it by the paper's rule (keep the leading
+                                decimal digit, divide by ten: 800x800 -> 60000)          */
+} gs_opt_config;
+
+/* Pinhole camera of the current view: p = R mu + t (R row-major,
+ * world -> camera, camera looking down +z).  A mean is visible iff
+ * z_near <= p.z <= z_far, |p.x| <= p.z tan_half_fovx, |p.y| <= p.z tan_half_fovy,
+ * evaluated in FP32 with every product rounded before it is summed, sums taken
+ * left to right ((R0 mu0 + R1 mu1) + R2 mu2) + t0, and no fused multiply-add. */
+typedef struct gs_camera {
+    float R[9];
+    float t[3];
+    float tan_half_fovx, tan_half_fovy, znear, zfar;
+} gs_camera;
+
+/* Per-iteration parameters. */
+typedef struct gs_step_params {
+    float lr[6];             /* xyz, scale, rot, opacity, SH DC (sh cols 0-2), SH rest   */
+    int32_t dar_opacity;     /* apply the opacity regulariser this step                   */
+    int32_t dar_scale;       /* apply the scale regulariser this step                     */
+    int32_t restate;         /* apply RSR to the StSS-sampled rows after this step        */
+    int32_t reserved;        /* must be 0                                                  */
+    double restate_ratio;    /* StSS sampling probability in [0, 1]                        */
+    uint64_t seed;           /* StSS stream seed                                           */
+    int64_t iteration;       /* global iteration k >= 1: keys the StSS draw (row sampled iff
+                                the top 53 bits of SplitMix64(seed, counter k<<32 | row),
+                                read as a fraction of 2^53, are below restate_ratio), and is
+                                the bias-correction step when bias_mode = 1                */
+    int64_t n_visible;       /* N_v for GS_REG_COUPLED (host-known visible count), else 0  */
+} gs_step_params;
+
+typedef struct gs_opt gs_opt;   /* opaque context */
+
+/* Name of a status code (static string). */
+const char *gs_status_string(gs_status s);
+
+/* GS_ABI_VERSION of the loaded library. */
+int32_t gs_abi_version(void);
+
+/* N_I of App. "DAR": the leading decimal digit of n_pixels kept, divided by
+ * ten (640000 -> 60000).  0 for n_pixels <= 0. */
+double gs_dar_normaliser(int64_t n_pixels);
+
+/*
+ * Create a context for n_rows primitives (0 <= n_rows < 2^31 - 1).
+ * Allocates and zeroes the library-owned state on the current CUDA device:
+ * moments m, v in the configured precision, per-primitive step counters t
+ * (all start at 0, as for newly created primitives, App. "Scaling in RSR"
+ * item 1), and the FP64 bias-correction table 1 - beta^k computed on the GPU.
+ * *out receives the context (NULL on failure).  Errors: GS_ERR_INVALID_ARG
+ * (config out of range, reserved fields non-zero), GS_ERR_OOM, GS_ERR_CUDA.
+ */
+gs_status gs_opt_init(gs_opt **out, const gs_opt_config *cfg, int64_t n_rows, void *stream);
+
+/* Free the context and its device memory (synchronises the device first).
+ * NULL is ignored. */
+void gs_opt_destroy(gs_opt *opt);
+
+/* Current row count (changes with gs_reindex_state), -1 for NULL. */
+int64_t gs_opt_rows(const gs_opt *opt);
+
+/*
+ * Visibility filter V of Eq. meth::sparse_beta for the view `cam`: the
+ * frustum test of each mean (see gs_camera).
+ *   xyz          device [n_rows][3] float32 means, read-only.
+ *   mask         device [n_rows] uint8 out: 1 visible, 0 not.  Required.
+ *   visible_rows device [n_rows] int32 out, optional (NULL): the visible row
+ *                indices, compacted (ascending within each tile of rows,
+ *                tiles in completion order).
+ *   n_visible    device int64 out, optional (NULL): the visible count; required
+ *                when visible_rows is given.
+ */
+gs_status gs_visibility(gs_opt *opt, const float *xyz, const gs_camera *cam, uint8_t *mask,
+                        int32_t *visible_rows, int64_t *n_visible, void *stream);
+
+/*
+ * One AdamW-GS step over the rows whose mask byte is non-zero.
+ *   attrs  device attribute groups, updated in place for visible rows only.
+ *   grads  device photometric gradients (the mean-loss gradient, i.e. already
+ *          divided by N_I as a renderer returns it), same layout; read for
+ *          visible rows only.
+ *   mask   device [n_rows] uint8 visibility (e.g. from gs_visibility or a
+ *          rasterizer's radii > 0); NULL = every row visible (dense Adam).
+ * Visible row: t += 1; m, v updated by Eq. disentangled_mom; theta moved by
+ * Eq. disentangled_adam with the bias-corrected moments of this step and the
+ * regulariser evaluated at the attribute before the update.  Invisible row:
+ * attributes, m, v, t untouched (beta' = 1).  If params->restate, every row
+ * the StSS draw selects (visible or not) then has m *= alpha1, v *= alpha2
+ * (Eq. meth::restate).
+ */
+gs_status gs_step(gs_opt *opt, const gs_attrs *attrs, const gs_grads *grads, const uint8_t *mask,
+                  const gs_step_params *params, void *stream);
+
+/*
+ * gs_visibility followed by gs_step, fused into one pass over the rows:
+ * each tile of rows tests its means against `cam`, compacts its visible rows
+ * in shared memory and updates them.
+ *   mask_out   device [n_rows] uint8 out, optional (NULL).
+ *   n_visible  device int64, optional (NULL): this step's visible count is
+ *              ADDED to it (atomically); zero it beforehand for a plain count.
+ */
+gs_status gs_step_camera(gs_opt *opt, const gs_attrs *attrs, const gs_grads *grads,
+                         const gs_camera *cam, uint8_t *mask_out, int64_t *n_visible,
+                         const gs_step_params *params, void *stream);
+
+/*
+ * gs_step_camera with the gradients in HOST memory: copies the five gradient
+ * groups into a library-owned device staging buffer on `stream`, runs the
+ * fused step, copies the visible count back to *n_visible_host and
+ * synchronises `stream` before returning (blocking).  Pinned host memory
+ * makes the copies run at full link speed.
+ */
+gs_status gs_step_host(gs_opt *opt, const gs_attrs *attrs, const gs_grads *grads_host,
+                       const gs_camera *cam, const gs_step_params *params,
+                       int64_t *n_visible_host, void *stream);
+
+/*
+ * Re-index the optimizer state for a new primitive set of n_new rows
+ * (densify / prune / relocate).  Output row j inherits the state of old row
+ * src_rows[j]; src_rows[j] < 0, or reset[j] != 0, starts it at zero m, v and
+ * t = 0 (a new or relocated primitive).  Re-indexing the attribute arrays is
+ * the caller's job (or gs_gather_attrs).
+ *   src_rows device [n_new] int32, read-only; values must be < the old row count.
+ *   reset    device [n_new] uint8, optional (NULL).
+ * A source index out of range is not read: that row is zeroed and the
+ * context records GS_ERR_INVALID_ARG, returned by the next gs_opt_sync_errors.
+ * 0 <= n_new < 2^31 - 1; the state grows if needed (allocation is synchronous).
+ */
+gs_status gs_reindex_state(gs_opt *opt, const int32_t *src_rows, const uint8_t *reset,
+                           int64_t n_new, void *stream);
+
+/*
+ * Gather attribute rows for a new primitive set: out row j = in row
+ * src_rows[j] for every group (src_rows[j] must be in [0, n_in)); a negative
+ * entry leaves out row j untouched.  in and out are distinct device buffers
+ * of n_in and n_new rows.  Out-of-range sources are skipped and recorded as
+ * for gs_reindex_state.
+ */
+gs_status gs_gather_attrs(gs_opt *opt, const gs_attrs *in, int64_t n_in, const gs_attrs *out,
+                          const int32_t *src_rows, int64_t n_new, void *stream);
+
+/*
+ * Copy the state out in the canonical layout (float32 m, v [n_rows][59] in
+ * the column order xyz, scale, rot, opacity, sh; uint32 t [n_rows]), decoding
+ * low-precision moments.  Any of m, v, t may be NULL.  Device buffers.
+ */
+gs_status gs_opt_export_state(gs_opt *opt, float *m, float *v, uint32_t *t, void *stream);
+
+/* Inverse of gs_opt_export_state (checkpoint resume); NULL leaves that part
+ * unchanged.  Low-precision moments are re-encoded. */
+gs_status gs_opt_import_state(gs_opt *opt, const float *m, const float *v, const uint32_t *t,
+                              void *stream);
+
+/* Length of the context's bias-correction table: the first step count k at
+ * which both FP32 factors 1/(1 - beta1^k) and 1/sqrt(1 - beta2^k) round to
+ * exactly 1 (15 936 for beta2 = 0.999), at most 2^22.  -1 for NULL. */
+int64_t gs_bias_table_len(const gs_opt *opt);
+
+/* Copy the FP64 bias-correction denominators 1 - beta1^k, 1 - beta2^k for
+ * k = 0 .. len-1 (computed on the GPU at init, beta^k by binary
+ * exponentiation) into device buffers; len <= gs_bias_table_len(opt). */
+gs_status gs_bias_table(gs_opt *opt, double *one_minus_b1k, double *one_minus_b2k, int64_t len,
+                        void *stream);
+
+/* Synchronise `stream` and return (then clear) the first error recorded by a
+ * device-side check since the last call, GS_OK if none. */
+gs_status gs_opt_sync_errors(gs_opt *opt, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GSOPT_H */

@@ -1,0 +1,224 @@
+// Kernels around the fused step: the standalone visibility filter with
+// global compaction, the FP64 bias-correction table, optimizer-state
+// re-indexing across row-set changes, canonical-layout export/import, and
+// the attribute gather that accompanies a re-index.
+
+#include "gs_internal.cuh"
+
+namespace gs {
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ void record_error(int32_t *err, int32_t code)
+{
+    if (err) atomicCAS(err, 0, code);
+}
+
+// ---------------------------------------------------------------- visibility
+// One thread per row decides V (frustum test of the mean); each CTA compacts
+// its visible rows with warp ballots, reserves a contiguous range of the
+// output list with one atomicAdd, and writes them in ascending row order.
+__global__ void __launch_bounds__(kThreads) visibility_kernel(const float *__restrict__ xyz, int32_t n,
+                                                              const gs_camera cam, uint8_t *__restrict__ mask,
+                                                              int32_t *__restrict__ list,
+                                                              unsigned long long *__restrict__ count)
+{
+    __shared__ int32_t s_cnt[kThreads / 32];
+    __shared__ unsigned long long s_base;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t row = (int64_t)blockIdx.x * kThreads + tid;
+    const float *c = reinterpret_cast<const float *>(&cam);
+    bool vis = false;
+    if (row < n) {
+        const float *p = xyz + row * 3;
+        vis = frustum_visible(p[0], p[1], p[2], c);
+        mask[row] = vis ? 1 : 0;
+    }
+    if (!count) return;
+    const unsigned b = __ballot_sync(0xffffffffu, vis);
+    if (lane == 0) s_cnt[warp] = __popc(b);
+    __syncthreads();
+    if (tid == 0) {
+        int tot = 0;
+        for (int q = 0; q < kThreads / 32; ++q) tot += s_cnt[q];
+        s_base = tot ? atomicAdd(count, (unsigned long long)tot) : 0ull;
+    }
+    __syncthreads();
+    if (list && vis) {
+        int off = 0;
+        for (int q = 0; q < warp; ++q) off += s_cnt[q];
+        off += __popc(b & ((1u << lane) - 1u));
+        list[s_base + off] = (int32_t)row;
+    }
+}
+
+// --------------------------------------------------------------- bias table
+// 1 - beta^k in FP64 for k = 0 .. len-1 (beta^k by binary exponentiation),
+// plus the FP32 factors the step consumes: 1/(1 - b1^k), 1/sqrt(1 - b2^k).
+__device__ double pow_int(double b, uint32_t e)
+{
+    double p = 1.0;
+    while (e) {
+        if (e & 1u) p *= b;
+        b *= b;
+        e >>= 1;
+    }
+    return p;
+}
+
+__global__ void bias_table_kernel(double beta1, double beta2, int32_t len, double *t1, double *t2,
+                                  float2 *fac)
+{
+    const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= len) return;
+    const double d1 = 1.0 - pow_int(beta1, (uint32_t)k);
+    const double d2 = 1.0 - pow_int(beta2, (uint32_t)k);
+    t1[k] = d1;
+    t2[k] = d2;
+    fac[k] = (k == 0) ? make_float2(0.0f, 0.0f) : make_float2((float)(1.0 / d1), (float)(1.0 / sqrt(d2)));
+}
+
+// ------------------------------------------------------------------ reindex
+// FP32 state: 16 threads per output row, one float4 each of slots 0..59
+// (slot 59 of m is the step counter, copied / zeroed with the moments).
+__global__ void reindex_f32_kernel(const float *__restrict__ m_in, const float *__restrict__ v_in, int32_t n_in,
+                                   float *__restrict__ m_out, float *__restrict__ v_out, int32_t n_out,
+                                   const int32_t *__restrict__ src, const uint8_t *__restrict__ reset,
+                                   int32_t *err)
+{
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t j = gid >> 4;
+    const int c = (int)(gid & 15);
+    if (j >= n_out || c >= 15) return;
+    int32_t s = src[j];
+    if (s >= n_in) {
+        if (c == 0) record_error(err, GS_ERR_INVALID_ARG);
+        s = -1;
+    }
+    const bool fresh = s < 0 || (reset && reset[j]);
+    float4 mv = make_float4(0.f, 0.f, 0.f, 0.f), vv = mv;
+    if (!fresh) {
+        mv = reinterpret_cast<const float4 *>(m_in + (size_t)s * kSlots)[c];
+        vv = reinterpret_cast<const float4 *>(v_in + (size_t)s * kSlots)[c];
+    }
+    reinterpret_cast<float4 *>(m_out + (size_t)j * kSlots)[c] = mv;
+    reinterpret_cast<float4 *>(v_out + (size_t)j * kSlots)[c] = vv;
+}
+
+// ------------------------------------------------------------ export/import
+__global__ void export_f32_kernel(const float *__restrict__ m, const float *__restrict__ v, int32_t n,
+                                  float *__restrict__ m_out, float *__restrict__ v_out, uint32_t *__restrict__ t_out)
+{
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (int64_t)n * kNumCols) return;
+    const int64_t r = gid / kNumCols;
+    const int c = (int)(gid - r * kNumCols);
+    const int s = slot_of_col(c);
+    if (m_out) m_out[gid] = m[r * kSlots + s];
+    if (v_out) v_out[gid] = v[r * kSlots + s];
+    if (t_out && c == 0) t_out[r] = reinterpret_cast<const uint32_t *>(m)[r * kSlots + kSlotT];
+}
+
+__global__ void import_f32_kernel(float *__restrict__ m, float *__restrict__ v, int32_t n,
+                                  const float *__restrict__ m_in, const float *__restrict__ v_in,
+                                  const uint32_t *__restrict__ t_in)
+{
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (int64_t)n * kNumCols) return;
+    const int64_t r = gid / kNumCols;
+    const int c = (int)(gid - r * kNumCols);
+    const int s = slot_of_col(c);
+    if (m_in) m[r * kSlots + s] = m_in[gid];
+    if (v_in) v[r * kSlots + s] = v_in[gid];
+    if (t_in && c == 0) reinterpret_cast<uint32_t *>(m)[r * kSlots + kSlotT] = t_in[r];
+}
+
+// ----------------------------------------------------------- attribute gather
+// One thread per (output row, canonical column).
+__global__ void gather_attrs_kernel(const gs_attrs in, int32_t n_in, const gs_attrs out,
+                                    const int32_t *__restrict__ src, int32_t n_new, int32_t *err)
+{
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (int64_t)n_new * kNumCols) return;
+    const int64_t j = gid / kNumCols;
+    const int c = (int)(gid - j * kNumCols);
+    const int32_t s = src[j];
+    if (s < 0) return;
+    if (s >= n_in) {
+        if (c == 0) record_error(err, GS_ERR_INVALID_ARG);
+        return;
+    }
+    const float *ip;
+    float *op;
+    int w, k;
+    if (c < 3) { ip = in.xyz; op = out.xyz; w = 3; k = c; }
+    else if (c < 6) { ip = in.scale; op = out.scale; w = 3; k = c - 3; }
+    else if (c < 10) { ip = in.rot; op = out.rot; w = 4; k = c - 6; }
+    else if (c == 10) { ip = in.opacity; op = out.opacity; w = 1; k = 0; }
+    else { ip = in.sh; op = out.sh; w = 48; k = c - 11; }
+    op[j * w + k] = ip[(int64_t)s * w + k];
+}
+
+unsigned blocks_for(int64_t n_threads) { return (unsigned)((n_threads + kThreads - 1) / kThreads); }
+
+}  // namespace
+
+cudaError_t launch_visibility(const float *xyz, int32_t n, const float cam[16], uint8_t *mask, int32_t *list,
+                              unsigned long long *count, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    gs_camera c;
+    memcpy(&c, cam, sizeof(c));
+    visibility_kernel<<<blocks_for(n), kThreads, 0, s>>>(xyz, n, c, mask, list, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bias_table(double beta1, double beta2, int32_t len, double *t1, double *t2, float2 *fac,
+                              cudaStream_t s)
+{
+    bias_table_kernel<<<blocks_for(len), kThreads, 0, s>>>(beta1, beta2, len, t1, t2, fac);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reindex(int prec, const void *m_in, const void *v_in, const float *, const float *, int32_t n_in,
+                           void *m_out, void *v_out, float *, float *, int32_t n_out, const int32_t *src,
+                           const uint8_t *reset, int32_t *err, cudaStream_t s)
+{
+    if (n_out <= 0) return cudaSuccess;
+    if (prec != GS_MOM_FP32) return cudaErrorNotSupported;
+    reindex_f32_kernel<<<blocks_for((int64_t)n_out * 16), kThreads, 0, s>>>(
+        static_cast<const float *>(m_in), static_cast<const float *>(v_in), n_in, static_cast<float *>(m_out),
+        static_cast<float *>(v_out), n_out, src, reset, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_export(int prec, const void *m, const void *v, const float *, const float *, int32_t n,
+                          float *m_out, float *v_out, uint32_t *t_out, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    if (prec != GS_MOM_FP32) return cudaErrorNotSupported;
+    export_f32_kernel<<<blocks_for((int64_t)n * kNumCols), kThreads, 0, s>>>(
+        static_cast<const float *>(m), static_cast<const float *>(v), n, m_out, v_out, t_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_import(int prec, void *m, void *v, float *, float *, int32_t n, const float *m_in,
+                          const float *v_in, const uint32_t *t_in, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    if (prec != GS_MOM_FP32) return cudaErrorNotSupported;
+    import_f32_kernel<<<blocks_for((int64_t)n * kNumCols), kThreads, 0, s>>>(
+        static_cast<float *>(m), static_cast<float *>(v), n, m_in, v_in, t_in);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_attrs(const gs_attrs &in, int32_t n_in, const gs_attrs &out, const int32_t *src,
+                                int32_t n_new, int32_t *err, cudaStream_t s)
+{
+    if (n_new <= 0) return cudaSuccess;
+    gather_attrs_kernel<<<blocks_for((int64_t)n_new * kNumCols), kThreads, 0, s>>>(in, n_in, out, src, n_new, err);
+    return cudaGetLastError();
+}
+
+}  // namespace gs

@@ -1,0 +1,159 @@
+// Internal declarations shared by the translation units of libgsopt.so:
+// the optimizer-state layout, the kernel argument block and the device-side
+// pieces of the method (frustum test, StSS draw, moment update).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <stdint.h>
+
+#include "gsopt.h"
+
+namespace gs {
+
+// ---------------------------------------------------------------- layout
+//
+// Optimizer state is library-owned, so it is laid out for the step kernel,
+// not in the caller's structure of arrays: one padded row of 64 slots per
+// primitive for m and one for v, so that a visible primitive's 59 moments
+// are one contiguous run of sectors (256 B in FP32) instead of five
+// scattered runs.  Slot order inside a row:
+//   0-47  SH (same column order as the sh group)
+//   48-51 rotation, 52-54 xyz, 55-57 scale, 58 opacity
+//   59    (m rows only) the primitive's step counter t as uint32 bits
+//   60-63 padding, never read
+// BF16 uses the same slots at 2 B each (128 B rows; t occupies slots 60-61
+// as one uint32 at byte 120 instead of slot 59).  FP8-e4m3 uses 1 B slots
+// (64 B rows; t at byte 60) with one FP32 scale per (256-row block, slot).
+constexpr int kSlots = 64;
+constexpr int kSlotSh = 0, kSlotRot = 48, kSlotXyz = 52, kSlotScale = 55, kSlotOpacity = 58;
+constexpr int kSlotT = 59;
+constexpr int kNumCols = 59;
+constexpr int kFp8Block = 256;
+
+// canonical column (xyz, scale, rot, opacity, sh) -> state slot
+__host__ __device__ inline int slot_of_col(int c)
+{
+    if (c < 3) return kSlotXyz + c;
+    if (c < 6) return kSlotScale + (c - 3);
+    if (c < 10) return kSlotRot + (c - 6);
+    if (c == 10) return kSlotOpacity;
+    return kSlotSh + (c - 11);
+}
+
+enum VisSource : int { kVisAll = 0, kVisMask = 1, kVisCamera = 2 };
+
+// ------------------------------------------------------------ arguments
+
+struct StepArgs {
+    float *a_xyz, *a_scale, *a_rot, *a_op, *a_sh;
+    const float *g_xyz, *g_scale, *g_rot, *g_op, *g_sh;
+    void *m, *v;                 // state rows
+    float *mscale, *vscale;      // FP8 block scales [n_blocks][64] (FP8 only)
+    const float2 *fac;           // per step count k: {1/(1-b1^k), 1/sqrt(1-b2^k)}
+    int32_t fac_len;             // factors are exactly 1.0f from here on
+    int32_t n_rows;
+    const uint8_t *mask_in;      // kVisMask
+    uint8_t *mask_out;           // optional
+    unsigned long long *n_visible;  // optional, accumulated with atomicAdd
+    int32_t *err;                // device error word (first error wins)
+    float cam[16];               // gs_camera as 16 floats
+    float lr[6];
+    float c1, c2;                // 1 - beta1, 1 - beta2 (FP32 of the FP64 values)
+    float eps;
+    float lam_o, lam_s;          // regulariser weights as the reg_mode consumes them
+    float clip_o, clip_s;
+    float alpha1, alpha2;
+    int32_t dar_o, dar_s, restate, bias_mode, reg_mode;
+    uint32_t k_bias;             // step used for bias correction when bias_mode == 1
+    uint64_t seed;
+    uint64_t k_ctr;              // StSS counter high word (the iteration k)
+    uint64_t rs_thr;             // row sampled iff (draw >> 11) < rs_thr
+};
+
+// ------------------------------------------------------- device helpers
+
+// Frustum test of one mean in FP32 with the exact rounding sequence the
+// ABI documents: each product rounded, sums left to right, no FMA.
+__device__ __forceinline__ bool frustum_visible(float x, float y, float z, const float *c)
+{
+    const float px = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[0], x), __fmul_rn(c[1], y)), __fmul_rn(c[2], z)), c[9]);
+    const float py = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[3], x), __fmul_rn(c[4], y)), __fmul_rn(c[5], z)), c[10]);
+    const float pz = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[6], x), __fmul_rn(c[7], y)), __fmul_rn(c[8], z)), c[11]);
+    const float wx = __fmul_rn(pz, c[12]);
+    const float wy = __fmul_rn(pz, c[13]);
+    return (pz >= c[14]) && (pz <= c[15]) && (fabsf(px) <= wx) && (fabsf(py) <= wy);
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014), counter-based: output number
+// `counter` of the stream seeded with `seed`.
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t counter)
+{
+    uint64_t z = seed + (counter + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// StSS membership of `row` at the sampling event a.k_ctr.
+__device__ __forceinline__ bool stss_sampled(const StepArgs &a, int32_t row)
+{
+    const uint64_t h = splitmix64_at(a.seed, (a.k_ctr << 32) | (uint64_t)(uint32_t)row);
+    return (h >> 11) < a.rs_thr;
+}
+
+// Derivative of the L1 regulariser through the opacity activation,
+// sig(tau)(1 - sig(tau)), written as e/(1+e)^2 with e = exp(-|tau|) so the
+// tails do not cancel (the two forms are equal for every tau).
+__device__ __forceinline__ float dsigmoid(float tau)
+{
+    const float e = expf(-fabsf(tau));
+    const float d = 1.0f + e;
+    return e / (d * d);
+}
+
+// One element of the step: moments (Eq. disentangled_mom, as the
+// equivalent update m += (1-b1)(g - m), v += (1-b2)(g^2 - v), which keeps the
+// FP32 decay exactly complementary to the FP32 gain), bias-corrected
+// direction m^/(sqrt(v^)+eps) (Eq. meth::adam_update) and the regulariser
+// term of the configured reg_mode (Eq. disentangled_adam for DAR).  Returns
+// the new attribute value.  `gr` is dR/dtheta at the old attribute; `has_reg`
+// selects whether this element carries a regulariser this step.
+__device__ __forceinline__ float step_element(float th, float g, float &m, float &v, float r1, float r2,
+                                              const StepArgs &a, float lr, bool has_reg, float gr,
+                                              float lam, float clip)
+{
+    if (has_reg && a.reg_mode == GS_REG_COUPLED) g = fmaf(lam, gr, g);
+    m = fmaf(a.c1, g - m, m);
+    v = fmaf(a.c2, fmaf(g, g, -v), v);
+    const float d = fmaf(sqrtf(v), r2, a.eps);
+    float u = (m * r1) / d;
+    if (has_reg) {
+        if (a.reg_mode == GS_REG_DAR) u += fminf((lam * gr) / d, clip);
+        else if (a.reg_mode == GS_REG_ADAMW) u += lam * gr;
+        else if (a.reg_mode == GS_REG_ADAMW_CLIP) u += fminf(lam * gr, clip);
+    }
+    return fmaf(-lr, u, th);
+}
+
+// --------------------------------------------------- launch entry points
+// (defined in the kernel translation units, called by api.cu)
+
+cudaError_t launch_step(const StepArgs &a, int prec, int vis_src, cudaStream_t s);
+cudaError_t launch_visibility(const float *xyz, int32_t n, const float cam[16], uint8_t *mask,
+                              int32_t *list, unsigned long long *count, cudaStream_t s);
+cudaError_t launch_bias_table(double beta1, double beta2, int32_t len, double *t1, double *t2,
+                              float2 *fac, cudaStream_t s);
+cudaError_t launch_reindex(int prec, const void *m_in, const void *v_in, const float *ms_in,
+                           const float *vs_in, int32_t n_in, void *m_out, void *v_out, float *ms_out,
+                           float *vs_out, int32_t n_out, const int32_t *src, const uint8_t *reset,
+                           int32_t *err, cudaStream_t s);
+cudaError_t launch_export(int prec, const void *m, const void *v, const float *ms, const float *vs,
+                          int32_t n, float *m_out, float *v_out, uint32_t *t_out, cudaStream_t s);
+cudaError_t launch_import(int prec, void *m, void *v, float *ms, float *vs, int32_t n,
+                          const float *m_in, const float *v_in, const uint32_t *t_in, cudaStream_t s);
+cudaError_t launch_gather_attrs(const gs_attrs &in, int32_t n_in, const gs_attrs &out,
+                                const int32_t *src, int32_t n_new, int32_t *err, cudaStream_t s);
+
+}  // namespace gs

@@ -1,0 +1,364 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (FP32 kernels vs FP64 oracle): per attribute group
+max|d| / max|ref| <= 1e-5 after one step and <= 1e-4 after 1000 steps;
+after one step also elementwise |d| <= 1e-5 (|ref| + 1e-3).  Visibility
+masks, compacted lists, counts, step counters and re-indexed state are
+compared bit-exactly.
+"""
+import numpy as np
+import pytest
+
+from harness import GpuRun, OracleRun, assert_close, group_errors
+from paper_2601_16736_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+LR = synth.lr_for_step(1, 10)
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_2601_16736_gb300 import build
+    build.build()
+    from paper_2601_16736_gb300 import gsopt
+    return gsopt
+
+
+# ------------------------------------------------------------- visibility
+
+@pytest.mark.parametrize("scene", ["uniform", "blobs"])
+def test_visibility_bit_exact(G, orc, scene):
+    n = 250_001
+    groups = synth.scene_uniform(n, 91) if scene == "uniform" else synth.scene_blobs(n, 92, 12.5)
+    xyz = torch.from_numpy(groups["xyz"]).cuda()
+    run = GpuRun(groups)
+    mask = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    rows = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    near = 0
+    for cam in synth.ring_cameras(6, (-30.0, 0.0, 30.0)):
+        G.gs_visibility(run.h, xyz, G.make_camera(cam), mask, rows, cnt)
+        torch.cuda.synchronize()
+        ref = orc.visibility_f32(groups["xyz"], cam)
+        got = mask.cpu().numpy()
+        assert np.array_equal(got, ref)
+        c = int(cnt.item())
+        assert c == int(ref.sum())
+        lst = rows.cpu().numpy()[:c]
+        assert np.array_equal(np.sort(lst), np.nonzero(ref)[0])
+        margin, mask64 = orc.frustum_margin_f64(groups["xyz"], cam)
+        near += int((np.abs(margin) < 1e-6).sum())
+        differ = mask64 != ref
+        assert np.all(np.abs(margin[differ]) < 1e-4), "FP32/FP64 decisions differ away from the planes"
+    print(f"rows within 1e-6 of a frustum plane (all views): {near}")
+    run.close()
+
+
+# ---------------------------------------------------------- one-step parity
+
+@pytest.mark.parametrize("scene,restate", [("uniform", False), ("blobs", True)])
+def test_one_step_parity(G, orc, scene, restate):
+    n = 100_003
+    groups = synth.scene_uniform(n, 101) if scene == "uniform" else synth.scene_blobs(n, 102, 12.5)
+    grads = synth.grads_rows(n, 103)
+    cam = synth.ring_cameras(8)[3]
+    run = GpuRun(groups)
+    run.set_grads(grads)
+    p = G.make_params(LR, 100, restate=restate, restate_ratio=0.3, seed=7)
+    run.step_camera(cam, p)
+    got = run.rows()
+    m, v, t = run.state()
+
+    ref = OracleRun(orc, synth.to_rows(groups))
+    vis = ref.visible(cam)
+    assert np.array_equal(run.mask.cpu().numpy(), vis)
+    assert int(run.nvis.item()) == int(vis.sum())
+    ref.st.t[:] = 0
+    ref.step(grads, vis, LR, True, True, 100, restate=restate, ratio=0.3, seed=7)
+    assert_close(got, ref.st.theta, 1e-5, 1e-5, what="theta")
+    assert_close(m, ref.st.m, 1e-5, what="m")
+    assert_close(v, ref.st.v, 1e-5, what="v")
+    assert np.array_equal(t, ref.st.t)
+    inv = vis == 0
+    assert np.array_equal(got[inv], synth.to_rows(groups)[inv])   # invisible rows untouched
+    run.close()
+
+
+@pytest.mark.parametrize("n", [1, 31, 33, 255, 257, 511, 512, 513, 1025, 1537])
+@pytest.mark.parametrize("pattern", ["all", "none", "one", "random"])
+def test_edge_sizes_and_masks(G, orc, n, pattern):
+    groups = synth.scene_uniform(n, 200 + n)
+    grads = synth.grads_rows(n, 300 + n)
+    grads[n // 2] = 0.0                                 # a visible row with zero gradient: v stays 0
+    rng = np.random.default_rng(n)
+    if pattern == "all":
+        mask_np = None
+    elif pattern == "none":
+        mask_np = np.zeros(n, np.uint8)
+    elif pattern == "one":
+        mask_np = np.zeros(n, np.uint8)
+        mask_np[n - 1] = 1
+    else:
+        mask_np = (rng.random(n) < 0.5).astype(np.uint8)
+    run = GpuRun(groups)
+    run.set_grads(grads)
+    ref = OracleRun(orc, synth.to_rows(groups))
+    mask_t = None if mask_np is None else torch.from_numpy(mask_np).cuda()
+    for k in (1, 2, 100):
+        p = G.make_params(LR, k, restate=(k == 100), restate_ratio=1.0 if n % 2 else 0.5, seed=11)
+        run.step_mask(mask_t, p)
+        ref.step(grads, mask_np, LR, True, True, k, restate=(k == 100), ratio=1.0 if n % 2 else 0.5, seed=11)
+    got = run.rows()
+    m, v, t = run.state()
+    assert_close(got, ref.st.theta, 1e-5, 1e-5, what="theta")
+    assert_close(m, ref.st.m, 1e-5, what="m")
+    assert_close(v, ref.st.v, 1e-5, what="v")
+    assert np.array_equal(t, ref.st.t)
+    if pattern == "none":
+        assert got.tobytes() == synth.to_rows(groups).tobytes()
+    run.close()
+
+
+def test_global_bias_mode(G, orc):
+    n = 5000
+    groups = synth.scene_blobs(n, 401, 12.5)
+    run = GpuRun(groups, bias_mode=1)
+    ref = OracleRun(orc, synth.to_rows(groups), bias_mode=1)
+    rng = np.random.default_rng(402)
+    for k in range(1, 31):
+        grads = synth.grads_rows(n, 403, k)
+        mask_np = (rng.random(n) < 0.3).astype(np.uint8)
+        run.set_grads(grads)
+        run.step_mask(torch.from_numpy(mask_np).cuda(), G.make_params(LR, k))
+        ref.step(grads, mask_np, LR, True, True, k)
+    assert_close(run.rows(), ref.st.theta, 1e-5, what="theta")
+
+
+@pytest.mark.parametrize("reg_mode", [1, 2, 3])
+def test_regulariser_variants(G, orc, reg_mode):
+    n = 4000
+    groups = synth.scene_uniform(n, 500 + reg_mode)
+    kw = dict(reg_mode=reg_mode)
+    if reg_mode == 3:
+        kw["lambda_o"] = 50.0                    # so the clip is active
+    run = GpuRun(groups, **kw)
+    ref = OracleRun(orc, synth.to_rows(groups), **kw)
+    rng = np.random.default_rng(600)
+    for k in range(1, 11):
+        grads = synth.grads_rows(n, 601, k)
+        mask_np = (rng.random(n) < 0.5).astype(np.uint8)
+        nv = int(mask_np.sum())
+        run.set_grads(grads)
+        run.step_mask(torch.from_numpy(mask_np).cuda(), G.make_params(LR, k, n_visible=nv))
+        ref.step(grads, mask_np, LR, True, True, k, n_visible=nv)
+    assert_close(run.rows(), ref.st.theta, 1e-5, what=f"reg_mode {reg_mode}")
+
+
+# ------------------------------------------------------------ multi-step
+
+def _run_sequence(G, orc, wl, n_steps, sample=None):
+    """Run n_steps of the workload's schedule on the GPU (all rows) and on the
+    oracle (all rows, or the `sample` of row ids); returns the comparison."""
+    groups = wl.scene_groups()
+    cams = wl.cameras()
+    order = synth.view_order(len(cams), n_steps, wl.seed)
+    n = wl.n
+    nbuf = wl.grad_buffers
+    grads_host = [synth.grads_rows(n, wl.seed, b) for b in range(nbuf)]
+    run = GpuRun(groups)
+    gdev = []
+    for gh in grads_host:
+        gdev.append({k: torch.from_numpy(v).cuda() for k, v in synth.from_rows(gh).items()})
+    ids = np.arange(n) if sample is None else np.asarray(sample)
+    ref = OracleRun(orc, synth.to_rows(groups)[ids], row_ids=ids)
+    diverged = np.zeros(ids.size, bool)
+    n_ambiguous = 0
+    for k in range(1, n_steps + 1):
+        cam = cams[order[k - 1]]
+        b = (k - 1) % nbuf
+        lr = synth.lr_for_step(k, n_steps)
+        rs = k % wl.restate_every == 0
+        p = G.make_params(lr, k, dar_opacity=wl.dar, dar_scale=wl.dar, restate=rs,
+                          restate_ratio=wl.restate_ratio, seed=wl.seed)
+        G.gs_step_camera(run.h, G.make_attrs(run.attrs), G.make_attrs(gdev[b]), G.make_camera(cam), p,
+                         mask_out=run.mask)
+        gmask = run.mask[torch.from_numpy(ids).cuda()].cpu().numpy() if sample is not None else run.mask.cpu().numpy()
+        omask = ref.visible(cam)
+        differ = gmask != omask
+        if differ.any():
+            margin, _ = orc.frustum_margin_f64(ref.st.theta[differ, 0:3].astype(np.float32), cam)
+            assert np.all(np.abs(margin) < 1e-4), "decision differs away from a frustum plane"
+            n_ambiguous += int(differ.sum())
+            diverged |= differ
+        ref.step(grads_host[b][ids], omask, lr, wl.dar, wl.dar, k,
+                 restate=rs, ratio=wl.restate_ratio, seed=wl.seed)
+    got = run.rows()[ids]
+    _, _, t = run.state()
+    keep = ~diverged
+    run.close()
+    return got, ref, t[ids], keep, n_ambiguous
+
+
+def test_multi_step_parity_small(G, orc):
+    wl = synth.Workload("small", 20_011, 300, 777, "blobs", extent=12.5,
+                        elevations=(-30.0, 0.0, 30.0), n_azimuth=20, grad_buffers=5)
+    got, ref, t, keep, amb = _run_sequence(G, orc, wl, 300)
+    assert keep.mean() > 0.999
+    assert_close(got, ref.st.theta, 1e-4, rows=keep, what="300 steps")
+    assert np.array_equal(t[keep], ref.st.t[keep])
+    print("ambiguous decisions:", amb, group_errors(got, ref.st.theta, rows=keep))
+
+
+def test_full_size_1000_steps_sampled(G, orc):
+    """The 1 M-primitive, 1000-step workload in the launch configuration the
+    bench times, checked on 3000 sampled primitives the oracle follows."""
+    wl = synth.WORKLOADS["c2_1m"]
+    sample = np.sort(np.random.default_rng(5).choice(wl.n, 3000, replace=False))
+    got, ref, t, keep, amb = _run_sequence(G, orc, wl, wl.steps, sample=sample)
+    assert keep.mean() > 0.998
+    errs = assert_close(got, ref.st.theta, 1e-4, rows=keep, what="1000 steps")
+    assert np.array_equal(t[keep], ref.st.t[keep])
+    print("ambiguous decisions:", amb, errs)
+
+
+# --------------------------------------------------------- state handling
+
+def _random_state(n, seed):
+    rng = np.random.default_rng(seed)
+    return (rng.normal(size=(n, 59)).astype(np.float32), rng.random((n, 59)).astype(np.float32),
+            rng.integers(0, 1000, n).astype(np.uint32))
+
+
+def test_export_import_roundtrip(G):
+    n = 3001
+    run = GpuRun(synth.scene_uniform(n, 700))
+    m, v, t = _random_state(n, 701)
+    G.gs_opt_import_state(run.h, torch.from_numpy(m).cuda(), torch.from_numpy(v).cuda(),
+                          torch.from_numpy(t.view(np.int32)).cuda())
+    m2, v2, t2 = run.state()
+    assert m2.tobytes() == m.tobytes() and v2.tobytes() == v.tobytes() and t2.tobytes() == t.tobytes()
+    run.close()
+
+
+@pytest.mark.parametrize("n_new_kind", ["same", "grow", "shrink"])
+def test_reindex_matches_oracle(G, orc, n_new_kind):
+    n = 50_000
+    run = GpuRun(synth.scene_uniform(n, 710))
+    m, v, t = _random_state(n, 711)
+    G.gs_opt_import_state(run.h, torch.from_numpy(m).cuda(), torch.from_numpy(v).cuda(),
+                          torch.from_numpy(t.view(np.int32)).cuda())
+    if n_new_kind == "same":
+        src, reset, _ = synth.reindex_event(n, 712, 0)
+    else:
+        n_new = n + 7777 if n_new_kind == "grow" else n - 7777
+        rng = np.random.default_rng(713)
+        src = rng.integers(-1, n, n_new).astype(np.int32)
+        reset = (rng.random(n_new) < 0.05).astype(np.uint8)
+    G.gs_reindex_state(run.h, torch.from_numpy(src).cuda(), torch.from_numpy(reset).cuda(), src.size)
+    run.n = src.size
+    assert G.gs_opt_rows(run.h) == src.size
+    m2, v2, t2 = run.state()
+    st = orc.State(np.zeros((n, 59)), m.astype(np.float64), v.astype(np.float64), t)
+    out = orc.reindex(st, src, reset)
+    assert np.array_equal(m2.astype(np.float64), out.m) and np.array_equal(v2.astype(np.float64), out.v)
+    assert np.array_equal(t2, out.t)
+    assert G.gs_opt_sync_errors(run.h) == G.GS_OK
+    run.close()
+
+
+def test_reindex_out_of_range_is_reported_not_read(G):
+    n = 1000
+    run = GpuRun(synth.scene_uniform(n, 720))
+    src = np.arange(n, dtype=np.int32)
+    src[17] = n + 5
+    G.gs_reindex_state(run.h, torch.from_numpy(src).cuda(), None, n)
+    assert G.gs_opt_sync_errors(run.h) == G.GS_ERR_INVALID_ARG
+    assert G.gs_opt_sync_errors(run.h) == G.GS_OK
+    _, _, t = run.state()
+    assert t[17] == 0
+    run.close()
+
+
+def test_gather_attrs(G):
+    n = 7001
+    groups = synth.scene_uniform(n, 730)
+    run = GpuRun(groups)
+    src, reset, attr_src = synth.reindex_event(n, 731, 0)
+    out = {k: torch.zeros((attr_src.size, v.shape[1]), dtype=torch.float32, device="cuda") for k, v in groups.items()}
+    G.gs_gather_attrs(run.h, G.make_attrs(run.attrs), n, G.make_attrs(out), torch.from_numpy(attr_src).cuda(),
+                      attr_src.size)
+    torch.cuda.synchronize()
+    for k, v in groups.items():
+        assert np.array_equal(out[k].cpu().numpy(), v[attr_src])
+    run.close()
+
+
+def test_bias_table_matches_oracle(G, orc):
+    run = GpuRun(synth.scene_uniform(10, 740))
+    L = G.gs_bias_table_len(run.h)
+    # first k at which both FP32 factors are exactly 1: 1/sqrt(1 - 0.999^k)
+    # rounds to 1.0f once 0.999^k <= 2^-23, i.e. from k ~ 15936 on
+    k = np.arange(1, 40000, dtype=np.float64)
+    f1 = (1.0 / (1.0 - 0.9 ** k)).astype(np.float32)
+    f2 = (1.0 / np.sqrt(1.0 - 0.999 ** k)).astype(np.float32)
+    first = int(k[np.nonzero((f1 == 1.0) & (f2 == 1.0))[0][0]])
+    assert abs(L - (first + 1)) <= 1
+    b1 = torch.zeros(L, dtype=torch.float64, device="cuda")
+    b2 = torch.zeros_like(b1)
+    G.gs_bias_table(run.h, b1, b2, L)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(b1.cpu().numpy()[1:], orc.bias_denominators(0.9, L)[1:], rtol=1e-13)
+    np.testing.assert_allclose(b2.cpu().numpy()[1:], orc.bias_denominators(0.999, L)[1:], rtol=1e-12)
+    run.close()
+
+
+def test_step_host_equals_device_path(G):
+    n = 20_000
+    groups = synth.scene_blobs(n, 750, 12.5)
+    grads = synth.grads_rows(n, 751)
+    cam = synth.ring_cameras(5)[2]
+    a, b = GpuRun(groups), GpuRun(groups)
+    a.set_grads(grads)
+    p = G.make_params(LR, 1)
+    a.step_camera(cam, p)
+    gh = {k: torch.from_numpy(v).pin_memory() for k, v in synth.from_rows(grads).items()}
+    nv = G.gs_step_host(b.h, G.make_attrs(b.attrs), G.make_attrs(gh), G.make_camera(cam), p)
+    assert nv == int(a.nvis.item())
+    assert a.rows().tobytes() == b.rows().tobytes()
+    a.close()
+    b.close()
+
+
+# ---------------------------------------------------------- argument checks
+
+def test_invalid_arguments_are_rejected(G):
+    n = 1000
+    groups = synth.scene_uniform(n, 760)
+    run = GpuRun(groups)
+    A, Gr = G.make_attrs(run.attrs), G.make_attrs(run.grads)
+    cam = G.make_camera(synth.ring_cameras(4)[0])
+    ok = G.make_params(LR, 1)
+    with pytest.raises(G.GsError):                             # iteration 0
+        G.gs_step_camera(run.h, A, Gr, cam, G.make_params(LR, 0))
+    with pytest.raises(G.GsError):                             # ratio out of range
+        G.gs_step_camera(run.h, A, Gr, cam, G.make_params(LR, 1, restate=True, restate_ratio=1.5))
+    host = {k: torch.from_numpy(v) for k, v in groups.items()}
+    with pytest.raises(G.GsError):                             # host memory as device attrs
+        G.gs_step_camera(run.h, G.make_attrs(host), Gr, cam, ok)
+    mis = dict(run.attrs)
+    buf = torch.zeros(n * 48 + 1, dtype=torch.float32, device="cuda")
+    mis["sh"] = buf[1:].view(n, 48)                              # 4-byte misaligned
+    with pytest.raises(G.GsError):
+        G.gs_step_camera(run.h, G.make_attrs(mis), Gr, cam, ok)
+    bad_cam = synth.ring_cameras(4)[0].copy()
+    bad_cam[3] = np.nan
+    with pytest.raises(G.GsError):
+        G.gs_step_camera(run.h, A, Gr, G.make_camera(bad_cam), ok)
+    G.gs_step_camera(run.h, A, Gr, cam, ok)                      # the valid call still works
+    torch.cuda.synchronize()
+    run.close()
