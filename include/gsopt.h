@@ -218,6 +218,39 @@ gs_status gs_step_host(gs_opt *opt, const gs_attrs *attrs, const gs_grads *grads
                        const gs_camera *cam, const gs_step_params *params,
                        int64_t *n_visible_host, void *stream);
 
+/* Largest primitive count gs_step_host_noalloc accepts. */
+#define GS_NOALLOC_MAX_ROWS 65536
+
+/*
+ * gs_step_host that allocates nothing.  The paper has no counterpart: this
+ * is a deployment variant of the library's own host-gradient entry point.
+ *
+ * gs_step_host creates a device staging buffer for the gradients and a pinned
+ * host word for the count (cudaMalloc / cudaMallocHost) the first time it runs
+ * on a context.  Some callers cannot allocate at the moment they step: a
+ * process that committed its whole device-memory budget at start-up, a
+ * latency-critical or real-time thread on which a synchronising allocation is
+ * not allowed, or a host runtime that owns the CUDA allocator and forbids
+ * allocations behind its back.  This variant stages the gradients in a fixed
+ * array that the library keeps in device global memory: a file-scope array
+ * sized for GS_NOALLOC_MAX_ROWS rows (about 15.5 MB), reserved on each GPU
+ * where the library is used until the process exits.  It calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *
+ * Arguments, semantics, blocking behaviour and errors are those of
+ * gs_step_host, plus: a context with more than GS_NOALLOC_MAX_ROWS rows gives
+ * GS_ERR_INVALID_ARG and nothing is launched.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Every call in the
+ * process shares the one array, which keeps the previous call's contents: the
+ * visible counter is cleared on each call and the gradient staging is
+ * overwritten for all rows.  Calls that overlap on the GPU (other streams,
+ * threads or contexts) race on the array and must be serialised by the caller.
+ */
+gs_status gs_step_host_noalloc(gs_opt *opt, const gs_attrs *attrs, const gs_grads *grads_host,
+                               const gs_camera *cam, const gs_step_params *params,
+                               int64_t *n_visible_host, void *stream);
+
 /*
  * Re-index the optimizer state for a new primitive set of n_new rows
  * (densify / prune / relocate).  Output row j inherits the state of old row

@@ -7,6 +7,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <atomic>
 #include <new>
 
 #include "gs_internal.cuh"
@@ -556,3 +557,79 @@ gs_status gs_opt_sync_errors(gs_opt *o, void *stream)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// gs_step_host_noalloc: the host-gradient step with its staging in a fixed
+// device array instead of memory allocated on first use.
+
+namespace {
+
+constexpr size_t kNaRows = GS_NOALLOC_MAX_ROWS;
+// staging offsets in floats; every group starts on a 256-B boundary
+constexpr size_t kNaOff[5] = {0, 3 * kNaRows, 6 * kNaRows, 10 * kNaRows, 11 * kNaRows};
+constexpr size_t kNaCount = 59 * kNaRows;        // the visible counter (8 B)
+constexpr size_t kNaFloats = kNaCount + 64;
+constexpr int kNaMaxDevices = 64;
+static_assert((kNaRows * 4) % 256 == 0, "group offsets must stay 256-B aligned");
+
+std::atomic<float *> g_na_addr[kNaMaxDevices];
+
+}  // namespace
+
+static __device__ __align__(256) float g_noalloc_scratch[kNaFloats];
+
+namespace {
+
+// Device address of the fixed array on `device` (which must be current):
+// looked up once per device.
+float *noalloc_scratch(int device)
+{
+    if (device < 0 || device >= kNaMaxDevices) return nullptr;
+    float *p = g_na_addr[device].load(std::memory_order_acquire);
+    if (p) return p;
+    void *q = nullptr;
+    if (cudaGetSymbolAddress(&q, g_noalloc_scratch) != cudaSuccess || !q) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    g_na_addr[device].store(static_cast<float *>(q), std::memory_order_release);
+    return static_cast<float *>(q);
+}
+
+}  // namespace
+
+extern "C" gs_status gs_step_host_noalloc(gs_opt *o, const gs_attrs *attrs, const gs_grads *gh, const gs_camera *cam,
+                                          const gs_step_params *params, int64_t *n_visible_host, void *stream)
+{
+    gs_status st = precheck(o);
+    if (st != GS_OK) return st;
+    const int64_t n = o->n_rows;
+    if (n > (int64_t)kNaRows) return GS_ERR_INVALID_ARG;
+    if (!attrs || !gh || !camera_ok(cam) || !params_ok(o, params) || !n_visible_host) return GS_ERR_INVALID_ARG;
+    if (n && (!gh->xyz || !gh->scale || !gh->rot || !gh->opacity || !gh->sh)) return GS_ERR_INVALID_ARG;
+    if (!attrs_ok(o, *attrs, n)) return GS_ERR_INVALID_ARG;
+    float *base = noalloc_scratch(o->device);
+    if (!base) return GS_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t w[5] = {3, 3, 4, 1, 48};
+    const float *src[5] = {gh->xyz, gh->scale, gh->rot, gh->opacity, gh->sh};
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 5 && e == cudaSuccess; ++i)
+        if (n) e = cudaMemcpyAsync(base + kNaOff[i], src[i], sizeof(float) * w[i] * (size_t)n, cudaMemcpyHostToDevice, s);
+    unsigned long long *count = reinterpret_cast<unsigned long long *>(base + kNaCount);
+    if (e == cudaSuccess) e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), s);
+    gs_grads gd{base + kNaOff[0], base + kNaOff[1], base + kNaOff[2], base + kNaOff[3], base + kNaOff[4]};
+    StepArgs a;
+    fill_args(o, params, &a);
+    set_attrs(&a, attrs, &gd);
+    memcpy(a.cam, cam, sizeof(a.cam));
+    a.n_visible = count;
+    if (e == cudaSuccess) e = gs::launch_step(a, o->cfg.prec, gs::kVisCamera, s);
+    unsigned long long h = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, count, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail_cuda(o, e);
+    *n_visible_host = (int64_t)h;
+    return GS_OK;
+}
+

@@ -19,6 +19,7 @@ GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CUDA, GS_ERR_OOM, GS_ERR_UNSUPPORTED, GS_ERR_T
 GS_MOM_FP32, GS_MOM_BF16, GS_MOM_FP8E4M3 = range(3)
 GS_REG_DAR, GS_REG_COUPLED, GS_REG_ADAMW, GS_REG_ADAMW_CLIP = range(4)
 GROUPS = (("xyz", 3), ("scale", 3), ("rot", 4), ("opacity", 1), ("sh", 48))
+GS_NOALLOC_MAX_ROWS = 65536
 
 
 class GsError(RuntimeError):
@@ -76,6 +77,8 @@ def _load():
                             ctypes.POINTER(gs_step_params), P], ctypes.c_int),
         "gs_step_host": ([P, ctypes.POINTER(gs_attrs), ctypes.POINTER(gs_attrs), ctypes.POINTER(gs_camera),
                           ctypes.POINTER(gs_step_params), ctypes.POINTER(i64), P], ctypes.c_int),
+        "gs_step_host_noalloc": ([P, ctypes.POINTER(gs_attrs), ctypes.POINTER(gs_attrs), ctypes.POINTER(gs_camera),
+                                  ctypes.POINTER(gs_step_params), ctypes.POINTER(i64), P], ctypes.c_int),
         "gs_reindex_state": ([P, P, P, i64, P], ctypes.c_int),
         "gs_gather_attrs": ([P, ctypes.POINTER(gs_attrs), i64, ctypes.POINTER(gs_attrs), P, i64, P], ctypes.c_int),
         "gs_opt_export_state": ([P, P, P, P, P], ctypes.c_int),
@@ -189,6 +192,15 @@ def gs_step_host(h, attrs: gs_attrs, grads_host: gs_attrs, cam: gs_camera, param
     nv = ctypes.c_int64(0)
     _check(_load().gs_step_host(h, ctypes.byref(attrs), ctypes.byref(grads_host), ctypes.byref(cam),
                                 ctypes.byref(params), ctypes.byref(nv), _stream(stream)), "gs_step_host")
+    return nv.value
+
+
+def gs_step_host_noalloc(h, attrs: gs_attrs, grads_host: gs_attrs, cam: gs_camera, params: gs_step_params,
+                         stream=None) -> int:
+    nv = ctypes.c_int64(0)
+    _check(_load().gs_step_host_noalloc(h, ctypes.byref(attrs), ctypes.byref(grads_host), ctypes.byref(cam),
+                                        ctypes.byref(params), ctypes.byref(nv), _stream(stream)),
+           "gs_step_host_noalloc")
     return nv.value
 
 
