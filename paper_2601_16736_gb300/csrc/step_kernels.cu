@@ -2,22 +2,23 @@
 // visible rows of a tile, Sparse Adam + DAR on the visible rows, RSR on the
 // StSS-sampled rows — one pass over HBM per step.
 //
-// Work decomposition (one CTA = one tile of kTile consecutive rows, 256
-// threads):
+// One CTA handles one tile of kTile consecutive rows with 256 threads:
 //   A. each thread decides visibility (camera frustum test of the mean,
-//      caller mask, or all-visible) and StSS membership for kTile/256 rows;
-//      warp ballots + a per-(chunk, warp) count table give every visible row
-//      its position in a shared-memory list, ascending by row.
-//   B. one thread per visible row reads its step counter and stages the two
-//      bias-correction factors in shared memory.
-//   C. a flat loop over work items: 12 SH items per visible row (one float4
-//      of 4 SH columns each — a warp covers 2.7 rows of contiguous 192-B SH
-//      rows and 256-B state rows), 1 item per visible row for the 11 small
-//      columns (xyz, scale, rotation, opacity: scalar / float4 loads of the
-//      caller's SoA groups, 3 float4 of the state row, DAR terms, t += 1),
-//      and 15 state-only items per invisible StSS-sampled row (RSR).
+//      caller mask, or all-visible) and StSS membership for kTile/256 rows,
+//      issuing the load of a visible row's step counter right away; warp
+//      ballots + a per-(chunk, warp) count table place every visible row in a
+//      shared-memory list (ascending by row) next to the two bias-correction
+//      factors of its new step count.
+//   B. a flat loop over work items, each one float4 of a state row (4 moment
+//      slots) with the 4 attribute columns that map to it:
+//        12 SH items per visible row (slots 0-47: a warp covers 2.7 rows of
+//           contiguous 192-B SH rows and 256-B state rows),
+//        1 rotation item (slots 48-51), 1 xyz + scale0 item (52-55),
+//        1 scale1 + scale2 + opacity + t item (56-59) per visible row,
+//        15 state-only RSR items per invisible StSS-sampled row.
+//      Items are grouped by kind so that warps stay convergent.
 // Every row's attributes, moments and counter are read and written by exactly
-// one thread per column group, once.
+// one item, once.
 
 #include "gs_internal.cuh"
 
@@ -31,42 +32,48 @@ __device__ __forceinline__ float4 ldg4_stream(const float *p)
 {
     return __ldcs(reinterpret_cast<const float4 *>(p));
 }
-__device__ __forceinline__ void st4(float *p, float4 x) { *reinterpret_cast<float4 *>(p) = x; }
+// results are not read again in this step: store them evict-first
+__device__ __forceinline__ void st4(float *p, float4 x) { __stcs(reinterpret_cast<float4 *>(p), x); }
 
-// ---------------------------------------------------------------- FP32 state
-struct StateF32 {
-    static __device__ __forceinline__ float *row(void *base, int32_t r)
-    {
-        return static_cast<float *>(base) + (size_t)r * kSlots;
-    }
-    static __device__ __forceinline__ uint32_t load_t(void *m, int32_t r)
-    {
-        return reinterpret_cast<const uint32_t *>(row(m, r))[kSlotT];
-    }
+__device__ __forceinline__ float *state_row(void *base, int32_t r)
+{
+    return static_cast<float *>(base) + (size_t)r * kSlots;
+}
+
+__device__ __forceinline__ void scale4(float4 &x, float s)
+{
+    x.x *= s; x.y *= s; x.z *= s; x.w *= s;
+}
+
+// Shared-memory lists of one tile.
+template <int kTile>
+struct TileLists {
+    int32_t list[kTile];      // visible rows, bit 31 = StSS-sampled
+    int32_t rlist[kTile];     // invisible StSS-sampled rows
+    float2 fac[kTile];        // bias factors of each visible row
+    int32_t cnt[2][kTile / 32];
 };
 
+// Phase A: decide visibility and StSS membership for the tile's rows, prefetch
+// the step counters of visible rows, and compact both row sets into `L`.
+// Returns the visible count in nv and the invisible-sampled count in nr.
 template <int kTile>
-__global__ void __launch_bounds__(kThreads) step_tile_f32(const StepArgs a, const int vis_src)
+__device__ __forceinline__ void tile_decide(const StepArgs &a, const int vis_src, const int64_t r0, TileLists<kTile> &L,
+                                            int &nv, int &nr)
 {
-    static_assert(kTile % kThreads == 0, "tile must be a multiple of the block");
-    constexpr int kRpt = kTile / kThreads;    // rows per thread in phase A
+    constexpr int kRpt = kTile / kThreads;
     constexpr int kWarps = kThreads / 32;
-
-    __shared__ int32_t s_list[kTile];         // visible rows, bit 31 = StSS-sampled
-    __shared__ int32_t s_rlist[kTile];        // invisible StSS-sampled rows
-    __shared__ float2 s_fac[kTile];
-    __shared__ int32_t s_cnt[2][kRpt * kWarps];
-
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t r0 = (int64_t)blockIdx.x * kTile;
-
-    // ---- A: decide and compact
+    const int nrow = (int)min((int64_t)kTile, (int64_t)a.n_rows - r0);
     unsigned bal_v[kRpt], bal_r[kRpt], bal_s[kRpt];
+    uint32_t t_old[kRpt];
 #pragma unroll
     for (int j = 0; j < kRpt; ++j) {
-        const int64_t row = r0 + j * kThreads + tid;
-        const bool in = row < a.n_rows;
+        const int lr = j * kThreads + tid;
+        const int64_t row = r0 + lr;
+        const bool in = lr < nrow;
         bool vis = false, smp = false;
+        t_old[j] = 0;
         if (in) {
             if (vis_src == kVisCamera) {
                 const float *p = a.a_xyz + row * 3;
@@ -76,6 +83,8 @@ __global__ void __launch_bounds__(kThreads) step_tile_f32(const StepArgs a, cons
             } else {
                 vis = true;
             }
+            if (vis && !a.bias_mode)
+                t_old[j] = reinterpret_cast<const uint32_t *>(state_row(a.m, (int32_t)row))[kSlotT];
             if (a.mask_out) a.mask_out[row] = vis ? 1 : 0;
             if (a.restate) smp = stss_sampled(a, (int32_t)row);
         }
@@ -83,16 +92,17 @@ __global__ void __launch_bounds__(kThreads) step_tile_f32(const StepArgs a, cons
         bal_s[j] = __ballot_sync(0xffffffffu, smp);
         bal_r[j] = bal_s[j] & ~bal_v[j];
         if (lane == 0) {
-            s_cnt[0][j * kWarps + warp] = __popc(bal_v[j]);
-            s_cnt[1][j * kWarps + warp] = __popc(bal_r[j]);
+            L.cnt[0][j * kWarps + warp] = __popc(bal_v[j]);
+            L.cnt[1][j * kWarps + warp] = __popc(bal_r[j]);
         }
     }
     __syncthreads();
-    int nv = 0, nr = 0;
+    nv = 0;
+    nr = 0;
 #pragma unroll 4
     for (int q = 0; q < kRpt * kWarps; ++q) {
-        nv += s_cnt[0][q];
-        nr += s_cnt[1][q];
+        nv += L.cnt[0][q];
+        nr += L.cnt[1][q];
     }
     const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
@@ -100,115 +110,132 @@ __global__ void __launch_bounds__(kThreads) step_tile_f32(const StepArgs a, cons
         const int me = j * kWarps + warp;
         int bv = 0, br = 0;
         for (int q = 0; q < me; ++q) {
-            bv += s_cnt[0][q];
-            br += s_cnt[1][q];
+            bv += L.cnt[0][q];
+            br += L.cnt[1][q];
         }
         const int32_t row = (int32_t)(r0 + j * kThreads + tid);
         if (bal_v[j] & (1u << lane)) {
             const bool smp = (bal_s[j] >> lane) & 1u;
-            s_list[bv + __popc(bal_v[j] & lt)] = row | (smp ? (int32_t)0x80000000 : 0);
+            const int pos = bv + __popc(bal_v[j] & lt);
+            L.list[pos] = row | (smp ? (int32_t)0x80000000 : 0);
+            const uint32_t tb = a.bias_mode ? a.k_bias : t_old[j] + 1u;
+            L.fac[pos] = (tb < (uint32_t)a.fac_len) ? a.fac[tb] : make_float2(1.0f, 1.0f);
         }
-        if (bal_r[j] & (1u << lane)) s_rlist[br + __popc(bal_r[j] & lt)] = row;
+        if (bal_r[j] & (1u << lane)) L.rlist[br + __popc(bal_r[j] & lt)] = row;
     }
     if (tid == 0 && a.n_visible && nv) atomicAdd(a.n_visible, (unsigned long long)nv);
     __syncthreads();
+}
 
-    // ---- B: per-row bias-correction factors
-    for (int j = tid; j < nv; j += kThreads) {
-        const int32_t row = s_list[j] & 0x7fffffff;
-        const uint32_t tnew = StateF32::load_t(a.m, row) + 1u;
-        const uint32_t tb = a.bias_mode ? a.k_bias : tnew;
-        s_fac[j] = (tb < (uint32_t)a.fac_len) ? a.fac[tb] : make_float2(1.0f, 1.0f);
-    }
-    __syncthreads();
+template <int kTile, int kMinBlocks>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) step_tile_f32(const StepArgs a, const int vis_src)
+{
+    static_assert(kTile % kThreads == 0, "tile must be a multiple of the block");
+    __shared__ TileLists<kTile> L;
+    const int tid = threadIdx.x;
+    const int64_t r0 = (int64_t)blockIdx.x * kTile;
+    int nv, nr;
+    tile_decide<kTile>(a, vis_src, r0, L, nv, nr);
+    const int32_t *s_list = L.list, *s_rlist = L.rlist;
+    const float2 *s_fac = L.fac;
 
-    // ---- C: flat work loop
-    const int n_sh = 12 * nv, n_vis = 13 * nv, n_all = 13 * nv + 15 * nr;
-    for (int w = tid; w < n_all; w += kThreads) {
-        if (w < n_sh) {
-            // 4 SH columns of one visible row
-            const int j = w / 12, c = w - j * 12;
+    // ---- B: flat work loop, items grouped by kind
+    const int e_sh = 12 * nv, e_vis = 15 * nv, e_all = e_vis + 15 * nr;
+    for (int w = tid; w < e_all; w += kThreads) {
+        if (w < e_vis) {
+            int j, c;
+            if (w < e_sh) {
+                j = w / 12;
+                c = w - j * 12;
+            } else {
+                const int q = w - e_sh;
+                j = q % nv;
+                c = 12 + q / nv;
+            }
             const int32_t e = s_list[j];
             const int32_t row = e & 0x7fffffff;
             const float2 f = s_fac[j];
-            const size_t off = (size_t)row * 48 + c * 4;
-            float4 th = ld4(a.a_sh + off);
-            const float4 g = ldg4_stream(a.g_sh + off);
-            float *mr = StateF32::row(a.m, row) + kSlotSh + c * 4;
-            float *vr = StateF32::row(a.v, row) + kSlotSh + c * 4;
+            float *mr = state_row(a.m, row) + c * 4;
+            float *vr = state_row(a.v, row) + c * 4;
             float4 m = ld4(mr), v = ld4(vr);
-            const float lr_dc = a.lr[4], lr_rest = a.lr[5];
-            th.x = step_element(th.x, g.x, m.x, v.x, f.x, f.y, a, c == 0 ? lr_dc : lr_rest, false, 0.f, 0.f, 0.f);
-            th.y = step_element(th.y, g.y, m.y, v.y, f.x, f.y, a, c == 0 ? lr_dc : lr_rest, false, 0.f, 0.f, 0.f);
-            th.z = step_element(th.z, g.z, m.z, v.z, f.x, f.y, a, c == 0 ? lr_dc : lr_rest, false, 0.f, 0.f, 0.f);
-            th.w = step_element(th.w, g.w, m.w, v.w, f.x, f.y, a, lr_rest, false, 0.f, 0.f, 0.f);
-            if (e < 0) {
-                m.x *= a.alpha1; m.y *= a.alpha1; m.z *= a.alpha1; m.w *= a.alpha1;
-                v.x *= a.alpha2; v.y *= a.alpha2; v.z *= a.alpha2; v.w *= a.alpha2;
+            if (c < 12) {
+                // 4 SH columns (column 4c .. 4c+3; 0-2 are the DC term)
+                const size_t off = (size_t)row * 48 + c * 4;
+                float4 th = ld4(a.a_sh + off);
+                const float4 g = ldg4_stream(a.g_sh + off);
+                const float l0 = c == 0 ? a.lr[4] : a.lr[5], l3 = a.lr[5];
+                th.x = step_element(th.x, g.x, m.x, v.x, f.x, f.y, a, l0, false, 0.f, 0.f, 0.f);
+                th.y = step_element(th.y, g.y, m.y, v.y, f.x, f.y, a, l0, false, 0.f, 0.f, 0.f);
+                th.z = step_element(th.z, g.z, m.z, v.z, f.x, f.y, a, l0, false, 0.f, 0.f, 0.f);
+                th.w = step_element(th.w, g.w, m.w, v.w, f.x, f.y, a, l3, false, 0.f, 0.f, 0.f);
+                st4(a.a_sh + off, th);
+            } else if (c == 12) {
+                // rotation quaternion
+                float *pt = a.a_rot + (size_t)row * 4;
+                float4 th = ld4(pt);
+                const float4 g = ldg4_stream(a.g_rot + (size_t)row * 4);
+                const float l = a.lr[2];
+                th.x = step_element(th.x, g.x, m.x, v.x, f.x, f.y, a, l, false, 0.f, 0.f, 0.f);
+                th.y = step_element(th.y, g.y, m.y, v.y, f.x, f.y, a, l, false, 0.f, 0.f, 0.f);
+                th.z = step_element(th.z, g.z, m.z, v.z, f.x, f.y, a, l, false, 0.f, 0.f, 0.f);
+                th.w = step_element(th.w, g.w, m.w, v.w, f.x, f.y, a, l, false, 0.f, 0.f, 0.f);
+                st4(pt, th);
+            } else if (c == 13) {
+                // xyz and the first log-scale component
+                float *px = a.a_xyz + (size_t)row * 3;
+                float *ps = a.a_scale + (size_t)row * 3;
+                const float *gx = a.g_xyz + (size_t)row * 3;
+                const float *gsp = a.g_scale + (size_t)row * 3;
+                float x0 = px[0], x1 = px[1], x2 = px[2], s0 = ps[0];
+                const float g0 = __ldcs(gx), g1 = __ldcs(gx + 1), g2 = __ldcs(gx + 2), gs0 = __ldcs(gsp);
+                const bool ds = a.dar_s != 0;
+                // scale: dR/dkappa = exp(kappa) at the old value (App. Eq. scale)
+                const float r0s = ds ? expf(s0) : 0.f;
+                x0 = step_element(x0, g0, m.x, v.x, f.x, f.y, a, a.lr[0], false, 0.f, 0.f, 0.f);
+                x1 = step_element(x1, g1, m.y, v.y, f.x, f.y, a, a.lr[0], false, 0.f, 0.f, 0.f);
+                x2 = step_element(x2, g2, m.z, v.z, f.x, f.y, a, a.lr[0], false, 0.f, 0.f, 0.f);
+                s0 = step_element(s0, gs0, m.w, v.w, f.x, f.y, a, a.lr[1], ds, r0s, a.lam_s, a.clip_s);
+                __stcs(px, x0); __stcs(px + 1, x1); __stcs(px + 2, x2);
+                __stcs(ps, s0);
+            } else {
+                // the other two log-scale components, the opacity logit, t
+                float *ps = a.a_scale + (size_t)row * 3;
+                float *po = a.a_op + row;
+                const float *gsp = a.g_scale + (size_t)row * 3;
+                const float *gop = a.g_op + row;
+                float s1 = ps[1], s2 = ps[2], op = *po;
+                const float gs1 = __ldcs(gsp + 1), gs2 = __ldcs(gsp + 2), go = __ldcs(gop);
+                const bool ds = a.dar_s != 0, dop = a.dar_o != 0;
+                const float r1s = ds ? expf(s1) : 0.f, r2s = ds ? expf(s2) : 0.f;
+                // opacity: dR/dtau = sig'(tau) at the old value (App. Eq. opacity)
+                const float rop = dop ? dsigmoid(op) : 0.f;
+                s1 = step_element(s1, gs1, m.x, v.x, f.x, f.y, a, a.lr[1], ds, r1s, a.lam_s, a.clip_s);
+                s2 = step_element(s2, gs2, m.y, v.y, f.x, f.y, a, a.lr[1], ds, r2s, a.lam_s, a.clip_s);
+                op = step_element(op, go, m.z, v.z, f.x, f.y, a, a.lr[3], dop, rop, a.lam_o, a.clip_o);
+                m.w = __uint_as_float(__float_as_uint(m.w) + 1u);     // t += 1
+                __stcs(ps + 1, s1); __stcs(ps + 2, s2);
+                __stcs(po, op);
+                if (e < 0) {     // RSR leaves t (m slot 59) and the unused v slot alone
+                    m.x *= a.alpha1; m.y *= a.alpha1; m.z *= a.alpha1;
+                    v.x *= a.alpha2; v.y *= a.alpha2; v.z *= a.alpha2;
+                }
+                st4(mr, m);
+                st4(vr, v);
+                continue;
             }
-            st4(a.a_sh + off, th);
+            if (e < 0) {         // RSR post-scale of a sampled visible row
+                scale4(m, a.alpha1);
+                scale4(v, a.alpha2);
+            }
             st4(mr, m);
             st4(vr, v);
-        } else if (w < n_vis) {
-            // the 11 small columns of one visible row + its step counter
-            const int j = w - n_sh;
-            const int32_t e = s_list[j];
-            const int32_t row = e & 0x7fffffff;
-            const float2 f = s_fac[j];
-            float *mr = StateF32::row(a.m, row);
-            float *vr = StateF32::row(a.v, row);
-            float4 m0 = ld4(mr + 48), m1 = ld4(mr + 52), m2 = ld4(mr + 56);
-            float4 v0 = ld4(vr + 48), v1 = ld4(vr + 52), v2 = ld4(vr + 56);
-            float4 rot = ld4(a.a_rot + (size_t)row * 4);
-            const float4 grot = ldg4_stream(a.g_rot + (size_t)row * 4);
-            float *px = a.a_xyz + (size_t)row * 3;
-            float *ps = a.a_scale + (size_t)row * 3;
-            const float *gx = a.g_xyz + (size_t)row * 3;
-            const float *gs = a.g_scale + (size_t)row * 3;
-            float x0 = px[0], x1 = px[1], x2 = px[2];
-            float s0 = ps[0], s1 = ps[1], s2 = ps[2];
-            float op = a.a_op[row];
-            const float gx0 = __ldcs(gx), gx1 = __ldcs(gx + 1), gx2 = __ldcs(gx + 2);
-            const float gs0 = __ldcs(gs), gs1 = __ldcs(gs + 1), gs2 = __ldcs(gs + 2);
-            const float gop = __ldcs(a.g_op + row);
-
-            const bool ds = a.dar_s != 0, dop = a.dar_o != 0;
-            const float lr_x = a.lr[0], lr_s = a.lr[1], lr_r = a.lr[2], lr_o = a.lr[3];
-            rot.x = step_element(rot.x, grot.x, m0.x, v0.x, f.x, f.y, a, lr_r, false, 0.f, 0.f, 0.f);
-            rot.y = step_element(rot.y, grot.y, m0.y, v0.y, f.x, f.y, a, lr_r, false, 0.f, 0.f, 0.f);
-            rot.z = step_element(rot.z, grot.z, m0.z, v0.z, f.x, f.y, a, lr_r, false, 0.f, 0.f, 0.f);
-            rot.w = step_element(rot.w, grot.w, m0.w, v0.w, f.x, f.y, a, lr_r, false, 0.f, 0.f, 0.f);
-            x0 = step_element(x0, gx0, m1.x, v1.x, f.x, f.y, a, lr_x, false, 0.f, 0.f, 0.f);
-            x1 = step_element(x1, gx1, m1.y, v1.y, f.x, f.y, a, lr_x, false, 0.f, 0.f, 0.f);
-            x2 = step_element(x2, gx2, m1.z, v1.z, f.x, f.y, a, lr_x, false, 0.f, 0.f, 0.f);
-            // scale: dR/dkappa = exp(kappa) at the old value (App. Eq. scale)
-            s0 = step_element(s0, gs0, m1.w, v1.w, f.x, f.y, a, lr_s, ds, ds ? expf(s0) : 0.f, a.lam_s, a.clip_s);
-            s1 = step_element(s1, gs1, m2.x, v2.x, f.x, f.y, a, lr_s, ds, ds ? expf(s1) : 0.f, a.lam_s, a.clip_s);
-            s2 = step_element(s2, gs2, m2.y, v2.y, f.x, f.y, a, lr_s, ds, ds ? expf(s2) : 0.f, a.lam_s, a.clip_s);
-            // opacity: dR/dtau = sig'(tau) at the old value (App. Eq. opacity)
-            op = step_element(op, gop, m2.z, v2.z, f.x, f.y, a, lr_o, dop, dop ? dsigmoid(op) : 0.f, a.lam_o, a.clip_o);
-            m2.w = __uint_as_float(__float_as_uint(m2.w) + 1u);    // t += 1
-            if (e < 0) {
-                m0.x *= a.alpha1; m0.y *= a.alpha1; m0.z *= a.alpha1; m0.w *= a.alpha1;
-                m1.x *= a.alpha1; m1.y *= a.alpha1; m1.z *= a.alpha1; m1.w *= a.alpha1;
-                m2.x *= a.alpha1; m2.y *= a.alpha1; m2.z *= a.alpha1;
-                v0.x *= a.alpha2; v0.y *= a.alpha2; v0.z *= a.alpha2; v0.w *= a.alpha2;
-                v1.x *= a.alpha2; v1.y *= a.alpha2; v1.z *= a.alpha2; v1.w *= a.alpha2;
-                v2.x *= a.alpha2; v2.y *= a.alpha2; v2.z *= a.alpha2;
-            }
-            st4(a.a_rot + (size_t)row * 4, rot);
-            px[0] = x0; px[1] = x1; px[2] = x2;
-            ps[0] = s0; ps[1] = s1; ps[2] = s2;
-            a.a_op[row] = op;
-            st4(mr + 48, m0); st4(mr + 52, m1); st4(mr + 56, m2);
-            st4(vr + 48, v0); st4(vr + 52, v1); st4(vr + 56, v2);
         } else {
             // RSR on one float4 of an invisible sampled row (slot 59 of m is t)
-            const int q = w - n_vis;
+            const int q = w - e_vis;
             const int j = q / 15, c = q - j * 15;
             const int32_t row = s_rlist[j];
-            float *mr = StateF32::row(a.m, row) + c * 4;
-            float *vr = StateF32::row(a.v, row) + c * 4;
+            float *mr = state_row(a.m, row) + c * 4;
+            float *vr = state_row(a.v, row) + c * 4;
             float4 m = ld4(mr), v = ld4(vr);
             m.x *= a.alpha1; m.y *= a.alpha1; m.z *= a.alpha1;
             v.x *= a.alpha2; v.y *= a.alpha2; v.z *= a.alpha2;
@@ -221,7 +248,8 @@ __global__ void __launch_bounds__(kThreads) step_tile_f32(const StepArgs a, cons
 
 }  // namespace
 
-constexpr int kStepTile = 512;
+constexpr int kStepTile = 256;
+constexpr int kStepMinBlocks = 4;      // 64 registers: 4 CTAs of 256 threads per SM
 
 cudaError_t launch_step(const StepArgs &a, int prec, int vis_src, cudaStream_t s)
 {
@@ -229,7 +257,7 @@ cudaError_t launch_step(const StepArgs &a, int prec, int vis_src, cudaStream_t s
     const unsigned grid = (unsigned)((a.n_rows + kStepTile - 1) / kStepTile);
     switch (prec) {
     case GS_MOM_FP32:
-        step_tile_f32<kStepTile><<<grid, kThreads, 0, s>>>(a, vis_src);
+        step_tile_f32<kStepTile, kStepMinBlocks><<<grid, kThreads, 0, s>>>(a, vis_src);
         break;
     default:
         return cudaErrorNotSupported;
