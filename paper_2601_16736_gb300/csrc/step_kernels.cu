@@ -45,6 +45,100 @@ __device__ __forceinline__ void scale4(float4 &x, float s)
     x.x *= s; x.y *= s; x.z *= s; x.w *= s;
 }
 
+// One visible-row item: state chunk c (0..14) of `row` with its 4 attribute
+// columns; `sampled` applies the RSR post-scale; f = the row's bias factors.
+__device__ __forceinline__ void visible_item(const StepArgs &a, const int32_t row, const int c, const bool sampled,
+                                             const float2 f)
+{
+    float *mr = state_row(a.m, row) + c * 4;
+    float *vr = state_row(a.v, row) + c * 4;
+    float4 m = ld4(mr), v = ld4(vr);
+    if (c < 12) {
+        // 4 SH columns (column 4c .. 4c+3; 0-2 are the DC term)
+        const size_t off = (size_t)row * 48 + c * 4;
+        float4 th = ld4(a.a_sh + off);
+        const float4 g = ldg4_stream(a.g_sh + off);
+        const float l0 = c == 0 ? a.lr[4] : a.lr[5], l3 = a.lr[5];
+        th.x = step_element(th.x, g.x, m.x, v.x, f.x, f.y, a, l0, false, 0.f, 0.f, 0.f);
+        th.y = step_element(th.y, g.y, m.y, v.y, f.x, f.y, a, l0, false, 0.f, 0.f, 0.f);
+        th.z = step_element(th.z, g.z, m.z, v.z, f.x, f.y, a, l0, false, 0.f, 0.f, 0.f);
+        th.w = step_element(th.w, g.w, m.w, v.w, f.x, f.y, a, l3, false, 0.f, 0.f, 0.f);
+        st4(a.a_sh + off, th);
+    } else if (c == 12) {
+        // rotation quaternion
+        float *pt = a.a_rot + (size_t)row * 4;
+        float4 th = ld4(pt);
+        const float4 g = ldg4_stream(a.g_rot + (size_t)row * 4);
+        const float l = a.lr[2];
+        th.x = step_element(th.x, g.x, m.x, v.x, f.x, f.y, a, l, false, 0.f, 0.f, 0.f);
+        th.y = step_element(th.y, g.y, m.y, v.y, f.x, f.y, a, l, false, 0.f, 0.f, 0.f);
+        th.z = step_element(th.z, g.z, m.z, v.z, f.x, f.y, a, l, false, 0.f, 0.f, 0.f);
+        th.w = step_element(th.w, g.w, m.w, v.w, f.x, f.y, a, l, false, 0.f, 0.f, 0.f);
+        st4(pt, th);
+    } else if (c == 13) {
+        // xyz and the first log-scale component
+        float *px = a.a_xyz + (size_t)row * 3;
+        float *ps = a.a_scale + (size_t)row * 3;
+        const float *gx = a.g_xyz + (size_t)row * 3;
+        const float *gsp = a.g_scale + (size_t)row * 3;
+        float x0 = px[0], x1 = px[1], x2 = px[2], s0 = ps[0];
+        const float g0 = __ldcs(gx), g1 = __ldcs(gx + 1), g2 = __ldcs(gx + 2), gs0 = __ldcs(gsp);
+        const bool ds = a.dar_s != 0;
+        // scale: dR/dkappa = exp(kappa) at the old value (App. Eq. scale)
+        const float r0s = ds ? expf(s0) : 0.f;
+        x0 = step_element(x0, g0, m.x, v.x, f.x, f.y, a, a.lr[0], false, 0.f, 0.f, 0.f);
+        x1 = step_element(x1, g1, m.y, v.y, f.x, f.y, a, a.lr[0], false, 0.f, 0.f, 0.f);
+        x2 = step_element(x2, g2, m.z, v.z, f.x, f.y, a, a.lr[0], false, 0.f, 0.f, 0.f);
+        s0 = step_element(s0, gs0, m.w, v.w, f.x, f.y, a, a.lr[1], ds, r0s, a.lam_s, a.clip_s);
+        __stcs(px, x0); __stcs(px + 1, x1); __stcs(px + 2, x2);
+        __stcs(ps, s0);
+    } else {
+        // the other two log-scale components, the opacity logit, t
+        float *ps = a.a_scale + (size_t)row * 3;
+        float *po = a.a_op + row;
+        const float *gsp = a.g_scale + (size_t)row * 3;
+        const float *gop = a.g_op + row;
+        float s1 = ps[1], s2 = ps[2], op = *po;
+        const float gs1 = __ldcs(gsp + 1), gs2 = __ldcs(gsp + 2), go = __ldcs(gop);
+        const bool ds = a.dar_s != 0, dop = a.dar_o != 0;
+        const float r1s = ds ? expf(s1) : 0.f, r2s = ds ? expf(s2) : 0.f;
+        // opacity: dR/dtau = sig'(tau) at the old value (App. Eq. opacity)
+        const float rop = dop ? dsigmoid(op) : 0.f;
+        s1 = step_element(s1, gs1, m.x, v.x, f.x, f.y, a, a.lr[1], ds, r1s, a.lam_s, a.clip_s);
+        s2 = step_element(s2, gs2, m.y, v.y, f.x, f.y, a, a.lr[1], ds, r2s, a.lam_s, a.clip_s);
+        op = step_element(op, go, m.z, v.z, f.x, f.y, a, a.lr[3], dop, rop, a.lam_o, a.clip_o);
+        m.w = __uint_as_float(__float_as_uint(m.w) + 1u);     // t += 1
+        __stcs(ps + 1, s1); __stcs(ps + 2, s2);
+        __stcs(po, op);
+        if (sampled) {     // RSR leaves t (m slot 59) and the unused v slot alone
+            m.x *= a.alpha1; m.y *= a.alpha1; m.z *= a.alpha1;
+            v.x *= a.alpha2; v.y *= a.alpha2; v.z *= a.alpha2;
+        }
+        st4(mr, m);
+        st4(vr, v);
+        return;
+    }
+    if (sampled) {         // RSR post-scale of a sampled visible row
+        scale4(m, a.alpha1);
+        scale4(v, a.alpha2);
+    }
+    st4(mr, m);
+    st4(vr, v);
+}
+
+// RSR on state chunk c of an invisible StSS-sampled row (slot 59 of m is t).
+__device__ __forceinline__ void rsr_item(const StepArgs &a, const int32_t row, const int c)
+{
+    float *mr = state_row(a.m, row) + c * 4;
+    float *vr = state_row(a.v, row) + c * 4;
+    float4 m = ld4(mr), v = ld4(vr);
+    m.x *= a.alpha1; m.y *= a.alpha1; m.z *= a.alpha1;
+    v.x *= a.alpha2; v.y *= a.alpha2; v.z *= a.alpha2;
+    if (c != 14) { m.w *= a.alpha1; v.w *= a.alpha2; }
+    st4(mr, m);
+    st4(vr, v);
+}
+
 // Shared-memory lists of one tile.
 template <int kTile>
 struct TileLists {
@@ -153,95 +247,11 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) step_tile_f32(const Step
                 c = 12 + q / nv;
             }
             const int32_t e = s_list[j];
-            const int32_t row = e & 0x7fffffff;
-            const float2 f = s_fac[j];
-            float *mr = state_row(a.m, row) + c * 4;
-            float *vr = state_row(a.v, row) + c * 4;
-            float4 m = ld4(mr), v = ld4(vr);
-            if (c < 12) {
-                // 4 SH columns (column 4c .. 4c+3; 0-2 are the DC term)
-                const size_t off = (size_t)row * 48 + c * 4;
-                float4 th = ld4(a.a_sh + off);
-                const float4 g = ldg4_stream(a.g_sh + off);
-                const float l0 = c == 0 ? a.lr[4] : a.lr[5], l3 = a.lr[5];
-                th.x = step_element(th.x, g.x, m.x, v.x, f.x, f.y, a, l0, false, 0.f, 0.f, 0.f);
-                th.y = step_element(th.y, g.y, m.y, v.y, f.x, f.y, a, l0, false, 0.f, 0.f, 0.f);
-                th.z = step_element(th.z, g.z, m.z, v.z, f.x, f.y, a, l0, false, 0.f, 0.f, 0.f);
-                th.w = step_element(th.w, g.w, m.w, v.w, f.x, f.y, a, l3, false, 0.f, 0.f, 0.f);
-                st4(a.a_sh + off, th);
-            } else if (c == 12) {
-                // rotation quaternion
-                float *pt = a.a_rot + (size_t)row * 4;
-                float4 th = ld4(pt);
-                const float4 g = ldg4_stream(a.g_rot + (size_t)row * 4);
-                const float l = a.lr[2];
-                th.x = step_element(th.x, g.x, m.x, v.x, f.x, f.y, a, l, false, 0.f, 0.f, 0.f);
-                th.y = step_element(th.y, g.y, m.y, v.y, f.x, f.y, a, l, false, 0.f, 0.f, 0.f);
-                th.z = step_element(th.z, g.z, m.z, v.z, f.x, f.y, a, l, false, 0.f, 0.f, 0.f);
-                th.w = step_element(th.w, g.w, m.w, v.w, f.x, f.y, a, l, false, 0.f, 0.f, 0.f);
-                st4(pt, th);
-            } else if (c == 13) {
-                // xyz and the first log-scale component
-                float *px = a.a_xyz + (size_t)row * 3;
-                float *ps = a.a_scale + (size_t)row * 3;
-                const float *gx = a.g_xyz + (size_t)row * 3;
-                const float *gsp = a.g_scale + (size_t)row * 3;
-                float x0 = px[0], x1 = px[1], x2 = px[2], s0 = ps[0];
-                const float g0 = __ldcs(gx), g1 = __ldcs(gx + 1), g2 = __ldcs(gx + 2), gs0 = __ldcs(gsp);
-                const bool ds = a.dar_s != 0;
-                // scale: dR/dkappa = exp(kappa) at the old value (App. Eq. scale)
-                const float r0s = ds ? expf(s0) : 0.f;
-                x0 = step_element(x0, g0, m.x, v.x, f.x, f.y, a, a.lr[0], false, 0.f, 0.f, 0.f);
-                x1 = step_element(x1, g1, m.y, v.y, f.x, f.y, a, a.lr[0], false, 0.f, 0.f, 0.f);
-                x2 = step_element(x2, g2, m.z, v.z, f.x, f.y, a, a.lr[0], false, 0.f, 0.f, 0.f);
-                s0 = step_element(s0, gs0, m.w, v.w, f.x, f.y, a, a.lr[1], ds, r0s, a.lam_s, a.clip_s);
-                __stcs(px, x0); __stcs(px + 1, x1); __stcs(px + 2, x2);
-                __stcs(ps, s0);
-            } else {
-                // the other two log-scale components, the opacity logit, t
-                float *ps = a.a_scale + (size_t)row * 3;
-                float *po = a.a_op + row;
-                const float *gsp = a.g_scale + (size_t)row * 3;
-                const float *gop = a.g_op + row;
-                float s1 = ps[1], s2 = ps[2], op = *po;
-                const float gs1 = __ldcs(gsp + 1), gs2 = __ldcs(gsp + 2), go = __ldcs(gop);
-                const bool ds = a.dar_s != 0, dop = a.dar_o != 0;
-                const float r1s = ds ? expf(s1) : 0.f, r2s = ds ? expf(s2) : 0.f;
-                // opacity: dR/dtau = sig'(tau) at the old value (App. Eq. opacity)
-                const float rop = dop ? dsigmoid(op) : 0.f;
-                s1 = step_element(s1, gs1, m.x, v.x, f.x, f.y, a, a.lr[1], ds, r1s, a.lam_s, a.clip_s);
-                s2 = step_element(s2, gs2, m.y, v.y, f.x, f.y, a, a.lr[1], ds, r2s, a.lam_s, a.clip_s);
-                op = step_element(op, go, m.z, v.z, f.x, f.y, a, a.lr[3], dop, rop, a.lam_o, a.clip_o);
-                m.w = __uint_as_float(__float_as_uint(m.w) + 1u);     // t += 1
-                __stcs(ps + 1, s1); __stcs(ps + 2, s2);
-                __stcs(po, op);
-                if (e < 0) {     // RSR leaves t (m slot 59) and the unused v slot alone
-                    m.x *= a.alpha1; m.y *= a.alpha1; m.z *= a.alpha1;
-                    v.x *= a.alpha2; v.y *= a.alpha2; v.z *= a.alpha2;
-                }
-                st4(mr, m);
-                st4(vr, v);
-                continue;
-            }
-            if (e < 0) {         // RSR post-scale of a sampled visible row
-                scale4(m, a.alpha1);
-                scale4(v, a.alpha2);
-            }
-            st4(mr, m);
-            st4(vr, v);
+            visible_item(a, e & 0x7fffffff, c, e < 0, s_fac[j]);
         } else {
-            // RSR on one float4 of an invisible sampled row (slot 59 of m is t)
             const int q = w - e_vis;
             const int j = q / 15, c = q - j * 15;
-            const int32_t row = s_rlist[j];
-            float *mr = state_row(a.m, row) + c * 4;
-            float *vr = state_row(a.v, row) + c * 4;
-            float4 m = ld4(mr), v = ld4(vr);
-            m.x *= a.alpha1; m.y *= a.alpha1; m.z *= a.alpha1;
-            v.x *= a.alpha2; v.y *= a.alpha2; v.z *= a.alpha2;
-            if (c != 14) { m.w *= a.alpha1; v.w *= a.alpha2; }
-            st4(mr, m);
-            st4(vr, v);
+            rsr_item(a, s_rlist[j], c);
         }
     }
 }
