@@ -80,58 +80,112 @@ __global__ void bias_table_kernel(double beta1, double beta2, int32_t len, doubl
 }
 
 // ------------------------------------------------------------------ reindex
-// FP32 state: 16 threads per output row, one float4 each of slots 0..59
-// (slot 59 of m is the step counter, copied / zeroed with the moments).
-__global__ void reindex_f32_kernel(const float *__restrict__ m_in, const float *__restrict__ v_in, int32_t n_in,
-                                   float *__restrict__ m_out, float *__restrict__ v_out, int32_t n_out,
-                                   const int32_t *__restrict__ src, const uint8_t *__restrict__ reset,
-                                   int32_t *err)
+// One thread per (output row, 16-B chunk of its state): kChunks1 chunks of the
+// m and v rows (FP32: slots 0-59 incl. the counter; BF16: the whole 128-B row
+// incl. the counter at byte 120; hybrid: the 64-B FP32 row incl. the counter)
+// and kChunks2 chunks of the hybrid's 96-B BF16 SH rows.  Copied from row
+// src[j], or zeroed for a fresh row.
+template <int kChunks1, int kRowBytes1, int kChunks2, int kRowBytes2>
+__global__ void reindex_kernel(const StateView in, int32_t n_in, const StateView out, int32_t n_out,
+                               const int32_t *__restrict__ src, const uint8_t *__restrict__ reset, int32_t *err)
 {
+    constexpr int kPer = kChunks1 + kChunks2;
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t j = gid >> 4;
-    const int c = (int)(gid & 15);
-    if (j >= n_out || c >= 15) return;
+    const int64_t j = gid / kPer;
+    const int c = (int)(gid - j * kPer);
+    if (j >= n_out) return;
     int32_t s = src[j];
     if (s >= n_in) {
         if (c == 0) record_error(err, GS_ERR_INVALID_ARG);
         s = -1;
     }
     const bool fresh = s < 0 || (reset && reset[j]);
-    float4 mv = make_float4(0.f, 0.f, 0.f, 0.f), vv = mv;
+    const bool first = c < kChunks1;
+    const int cc = first ? c : c - kChunks1;
+    const int rb = first ? kRowBytes1 : kRowBytes2;
+    const char *im = static_cast<const char *>(first ? in.m : in.m2);
+    const char *iv = static_cast<const char *>(first ? in.v : in.v2);
+    char *om = static_cast<char *>(first ? out.m : out.m2);
+    char *ov = static_cast<char *>(first ? out.v : out.v2);
+    uint4 mv = make_uint4(0u, 0u, 0u, 0u), vv = mv;
     if (!fresh) {
-        mv = reinterpret_cast<const float4 *>(m_in + (size_t)s * kSlots)[c];
-        vv = reinterpret_cast<const float4 *>(v_in + (size_t)s * kSlots)[c];
+        mv = *reinterpret_cast<const uint4 *>(im + (size_t)s * rb + 16 * cc);
+        vv = *reinterpret_cast<const uint4 *>(iv + (size_t)s * rb + 16 * cc);
     }
-    reinterpret_cast<float4 *>(m_out + (size_t)j * kSlots)[c] = mv;
-    reinterpret_cast<float4 *>(v_out + (size_t)j * kSlots)[c] = vv;
+    *reinterpret_cast<uint4 *>(om + (size_t)j * rb + 16 * cc) = mv;
+    *reinterpret_cast<uint4 *>(ov + (size_t)j * rb + 16 * cc) = vv;
 }
 
 // ------------------------------------------------------------ export/import
-__global__ void export_f32_kernel(const float *__restrict__ m, const float *__restrict__ v, int32_t n,
-                                  float *__restrict__ m_out, float *__restrict__ v_out, uint32_t *__restrict__ t_out)
+// Canonical layout: [n][59] FP32 in the column order xyz, scale, rot,
+// opacity, sh; one thread per (row, column).
+
+// Where column c of row r of one moment (rows base, second rows base2)
+// lives: a pointer to an FP32 value, or (through *bf) to a BF16 value.
+__device__ __forceinline__ float *locate(const StateView &st, void *base, void *base2, int64_t r, int c,
+                                         __nv_bfloat16 **bf)
 {
-    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= (int64_t)n * kNumCols) return;
-    const int64_t r = gid / kNumCols;
-    const int c = (int)(gid - r * kNumCols);
-    const int s = slot_of_col(c);
-    if (m_out) m_out[gid] = m[r * kSlots + s];
-    if (v_out) v_out[gid] = v[r * kSlots + s];
-    if (t_out && c == 0) t_out[r] = reinterpret_cast<const uint32_t *>(m)[r * kSlots + kSlotT];
+    *bf = nullptr;
+    if (st.prec == GS_MOM_FP32) return static_cast<float *>(base) + r * kSlots + slot_of_col(c);
+    if (st.prec == GS_MOM_BF16) {
+        *bf = reinterpret_cast<__nv_bfloat16 *>(static_cast<char *>(base) + r * kRowBytesBf16) + slot_of_col(c);
+        return nullptr;
+    }
+    // hybrid FP32 row: [0-2] SH DC, [3] t, [4-7] rot, [8-10] xyz, [11-13] scale, [14] opacity
+    float *f = static_cast<float *>(base) + r * 16;
+    if (c < 3) return f + 8 + c;
+    if (c < 6) return f + 11 + (c - 3);
+    if (c < 10) return f + 4 + (c - 6);
+    if (c == 10) return f + 14;
+    if (c < 14) return f + (c - 11);
+    *bf = reinterpret_cast<__nv_bfloat16 *>(static_cast<char *>(base2) + r * kRowBytesHybSh) + (c - 11);
+    return nullptr;
 }
 
-__global__ void import_f32_kernel(float *__restrict__ m, float *__restrict__ v, int32_t n,
-                                  const float *__restrict__ m_in, const float *__restrict__ v_in,
-                                  const uint32_t *__restrict__ t_in)
+__device__ __forceinline__ uint32_t *t_of(const StateView &st, int64_t r)
+{
+    char *m = static_cast<char *>(st.m);
+    if (st.prec == GS_MOM_FP32) return reinterpret_cast<uint32_t *>(m + r * kRowBytesF32 + kTByteF32);
+    if (st.prec == GS_MOM_BF16) return reinterpret_cast<uint32_t *>(m + r * kRowBytesBf16 + kTByteBf16);
+    return reinterpret_cast<uint32_t *>(m + r * kRowBytesHyb + kTByteHyb);
+}
+
+__global__ void export_kernel(const StateView st, int32_t n, float *__restrict__ m_out, float *__restrict__ v_out,
+                              uint32_t *__restrict__ t_out)
 {
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= (int64_t)n * kNumCols) return;
     const int64_t r = gid / kNumCols;
     const int c = (int)(gid - r * kNumCols);
-    const int s = slot_of_col(c);
-    if (m_in) m[r * kSlots + s] = m_in[gid];
-    if (v_in) v[r * kSlots + s] = v_in[gid];
-    if (t_in && c == 0) reinterpret_cast<uint32_t *>(m)[r * kSlots + kSlotT] = t_in[r];
+    __nv_bfloat16 *b;
+    if (m_out) {
+        const float *p = locate(st, st.m, st.m2, r, c, &b);
+        m_out[gid] = p ? *p : __bfloat162float(*b);
+    }
+    if (v_out) {
+        const float *p = locate(st, st.v, st.v2, r, c, &b);
+        v_out[gid] = p ? *p : __bfloat162float(*b);
+    }
+    if (t_out && c == 0) t_out[r] = *t_of(st, r);
+}
+
+__global__ void import_kernel(const StateView st, int32_t n, const float *__restrict__ m_in,
+                              const float *__restrict__ v_in, const uint32_t *__restrict__ t_in)
+{
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (int64_t)n * kNumCols) return;
+    const int64_t r = gid / kNumCols;
+    const int c = (int)(gid - r * kNumCols);
+    __nv_bfloat16 *b;
+    if (m_in) {
+        float *p = locate(st, st.m, st.m2, r, c, &b);
+        if (p) *p = m_in[gid]; else *b = __float2bfloat16_rn(m_in[gid]);
+    }
+    if (v_in) {
+        float *p = locate(st, st.v, st.v2, r, c, &b);
+        if (p) *p = v_in[gid]; else *b = __float2bfloat16_rn(v_in[gid]);
+    }
+    if (t_in && c == 0) *t_of(st, r) = t_in[r];
 }
 
 // ----------------------------------------------------------- attribute gather
@@ -181,35 +235,42 @@ cudaError_t launch_bias_table(double beta1, double beta2, int32_t len, double *t
     return cudaGetLastError();
 }
 
-cudaError_t launch_reindex(int prec, const void *m_in, const void *v_in, const float *, const float *, int32_t n_in,
-                           void *m_out, void *v_out, float *, float *, int32_t n_out, const int32_t *src,
-                           const uint8_t *reset, int32_t *err, cudaStream_t s)
+cudaError_t launch_reindex(const StateView &in, int32_t n_in, const StateView &out, int32_t n_out,
+                           const int32_t *src, const uint8_t *reset, int32_t *err, cudaStream_t s)
 {
     if (n_out <= 0) return cudaSuccess;
-    if (prec != GS_MOM_FP32) return cudaErrorNotSupported;
-    reindex_f32_kernel<<<blocks_for((int64_t)n_out * 16), kThreads, 0, s>>>(
-        static_cast<const float *>(m_in), static_cast<const float *>(v_in), n_in, static_cast<float *>(m_out),
-        static_cast<float *>(v_out), n_out, src, reset, err);
+    switch (in.prec) {
+    case GS_MOM_FP32:
+        reindex_kernel<15, kRowBytesF32, 0, 16><<<blocks_for((int64_t)n_out * 15), kThreads, 0, s>>>(
+            in, n_in, out, n_out, src, reset, err);
+        break;
+    case GS_MOM_BF16:
+        reindex_kernel<8, kRowBytesBf16, 0, 16><<<blocks_for((int64_t)n_out * 8), kThreads, 0, s>>>(
+            in, n_in, out, n_out, src, reset, err);
+        break;
+    case GS_MOM_BF16_HYBRID:
+        reindex_kernel<4, kRowBytesHyb, 6, kRowBytesHybSh><<<blocks_for((int64_t)n_out * 10), kThreads, 0, s>>>(
+            in, n_in, out, n_out, src, reset, err);
+        break;
+    default:
+        return cudaErrorNotSupported;
+    }
     return cudaGetLastError();
 }
 
-cudaError_t launch_export(int prec, const void *m, const void *v, const float *, const float *, int32_t n,
-                          float *m_out, float *v_out, uint32_t *t_out, cudaStream_t s)
+cudaError_t launch_export(const StateView &st, int32_t n, float *m_out, float *v_out, uint32_t *t_out,
+                          cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    if (prec != GS_MOM_FP32) return cudaErrorNotSupported;
-    export_f32_kernel<<<blocks_for((int64_t)n * kNumCols), kThreads, 0, s>>>(
-        static_cast<const float *>(m), static_cast<const float *>(v), n, m_out, v_out, t_out);
+    export_kernel<<<blocks_for((int64_t)n * kNumCols), kThreads, 0, s>>>(st, n, m_out, v_out, t_out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_import(int prec, void *m, void *v, float *, float *, int32_t n, const float *m_in,
-                          const float *v_in, const uint32_t *t_in, cudaStream_t s)
+cudaError_t launch_import(const StateView &st, int32_t n, const float *m_in, const float *v_in,
+                          const uint32_t *t_in, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    if (prec != GS_MOM_FP32) return cudaErrorNotSupported;
-    import_f32_kernel<<<blocks_for((int64_t)n * kNumCols), kThreads, 0, s>>>(
-        static_cast<float *>(m), static_cast<float *>(v), n, m_in, v_in, t_in);
+    import_kernel<<<blocks_for((int64_t)n * kNumCols), kThreads, 0, s>>>(st, n, m_in, v_in, t_in);
     return cudaGetLastError();
 }
 

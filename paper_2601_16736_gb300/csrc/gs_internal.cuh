@@ -23,14 +23,20 @@ namespace gs {
 //   48-51 rotation, 52-54 xyz, 55-57 scale, 58 opacity
 //   59    (m rows only) the primitive's step counter t as uint32 bits
 //   60-63 padding, never read
-// BF16 uses the same slots at 2 B each (128 B rows; t occupies slots 60-61
-// as one uint32 at byte 120 instead of slot 59).  FP8-e4m3 uses 1 B slots
-// (64 B rows; t at byte 60) with one FP32 scale per (256-row block, slot).
+// BF16 uses the same slots at 2 B each (128-B rows; slot 59 unused, t is one
+// uint32 at byte 120, i.e. slots 60-61).
+// The BF16 hybrid stores each moment in two rows: an FP32 row of 16 slots
+// (64 B) for the 14 columns whose learning rate is large relative to their
+// magnitude — [0-2] SH DC, [3] t (m only), [4-7] rotation, [8-10] xyz,
+// [11-13] scale, [14] opacity, [15] unused — and a BF16 row of the 48 SH
+// columns (96 B; slots 0-2 unused, the DC moments live in the FP32 row).
 constexpr int kSlots = 64;
+constexpr int kRowBytesF32 = 256, kTByteF32 = 4 * 59;
+constexpr int kRowBytesBf16 = 128, kTByteBf16 = 120;
+constexpr int kRowBytesHyb = 64, kTByteHyb = 12, kRowBytesHybSh = 96;
 constexpr int kSlotSh = 0, kSlotRot = 48, kSlotXyz = 52, kSlotScale = 55, kSlotOpacity = 58;
 constexpr int kSlotT = 59;
 constexpr int kNumCols = 59;
-constexpr int kFp8Block = 256;
 
 // canonical column (xyz, scale, rot, opacity, sh) -> state slot
 __host__ __device__ inline int slot_of_col(int c)
@@ -50,7 +56,7 @@ struct StepArgs {
     float *a_xyz, *a_scale, *a_rot, *a_op, *a_sh;
     const float *g_xyz, *g_scale, *g_rot, *g_op, *g_sh;
     void *m, *v;                 // state rows
-    float *mscale, *vscale;      // FP8 block scales [n_blocks][64] (FP8 only)
+    void *m2, *v2;               // BF16 hybrid: the BF16 SH rows (m, v above are its FP32 rows)
     const float2 *fac;           // per step count k: {1/(1-b1^k), 1/sqrt(1-b2^k)}
     int32_t fac_len;             // factors are exactly 1.0f from here on
     int32_t n_rows;
@@ -145,14 +151,20 @@ cudaError_t launch_visibility(const float *xyz, int32_t n, const float cam[16], 
                               int32_t *list, unsigned long long *count, cudaStream_t s);
 cudaError_t launch_bias_table(double beta1, double beta2, int32_t len, double *t1, double *t2,
                               float2 *fac, cudaStream_t s);
-cudaError_t launch_reindex(int prec, const void *m_in, const void *v_in, const float *ms_in,
-                           const float *vs_in, int32_t n_in, void *m_out, void *v_out, float *ms_out,
-                           float *vs_out, int32_t n_out, const int32_t *src, const uint8_t *reset,
-                           int32_t *err, cudaStream_t s);
-cudaError_t launch_export(int prec, const void *m, const void *v, const float *ms, const float *vs,
-                          int32_t n, float *m_out, float *v_out, uint32_t *t_out, cudaStream_t s);
-cudaError_t launch_import(int prec, void *m, void *v, float *ms, float *vs, int32_t n,
-                          const float *m_in, const float *v_in, const uint32_t *t_in, cudaStream_t s);
+// State of one context as the kernels see it: m, v rows and, for the BF16
+// hybrid, its BF16 SH rows m2, v2.
+struct StateView {
+    int prec;
+    void *m, *v;
+    void *m2, *v2;
+};
+
+cudaError_t launch_reindex(const StateView &in, int32_t n_in, const StateView &out, int32_t n_out,
+                           const int32_t *src, const uint8_t *reset, int32_t *err, cudaStream_t s);
+cudaError_t launch_export(const StateView &st, int32_t n, float *m_out, float *v_out, uint32_t *t_out,
+                          cudaStream_t s);
+cudaError_t launch_import(const StateView &st, int32_t n, const float *m_in, const float *v_in,
+                          const uint32_t *t_in, cudaStream_t s);
 cudaError_t launch_gather_attrs(const gs_attrs &in, int32_t n_in, const gs_attrs &out,
                                 const int32_t *src, int32_t n_new, int32_t *err, cudaStream_t s);
 

@@ -9,16 +9,17 @@
 //      ballots + a per-(chunk, warp) count table place every visible row in a
 //      shared-memory list (ascending by row) next to the two bias-correction
 //      factors of its new step count.
-//   B. a flat loop over work items, each one float4 of a state row (4 moment
-//      slots) with the 4 attribute columns that map to it:
+//   B. a flat loop over work items, each one chunk of 4 state slots (4 moments
+//      of m and of v) with the 4 attribute columns that map to it:
 //        12 SH items per visible row (slots 0-47: a warp covers 2.7 rows of
-//           contiguous 192-B SH rows and 256-B state rows),
+//           contiguous 192-B SH rows and state rows),
 //        1 rotation item (slots 48-51), 1 xyz + scale0 item (52-55),
 //        1 scale1 + scale2 + opacity + t item (56-59) per visible row,
 //        15 state-only RSR items per invisible StSS-sampled row.
 //      Items are grouped by kind so that warps stay convergent.
 // Every row's attributes, moments and counter are read and written by exactly
-// one item, once.
+// one item, once.  The storage format of the moments is a template parameter
+// (State<kPrec>): all arithmetic is FP32.
 
 #include "gs_internal.cuh"
 
@@ -35,27 +36,193 @@ __device__ __forceinline__ float4 ldg4_stream(const float *p)
 // results are not read again in this step: store them evict-first
 __device__ __forceinline__ void st4(float *p, float4 x) { __stcs(reinterpret_cast<float4 *>(p), x); }
 
-__device__ __forceinline__ float *state_row(void *base, int32_t r)
+// ------------------------------------------------------------ state formats
+// A chunk of the state: 4 moments of m and of v as FP32, plus (chunk 14 only)
+// the row's step counter t.
+struct Chunk {
+    float4 m, v;
+    uint32_t t;
+};
+
+template <int kPrec>
+struct State;
+
+template <>
+struct State<GS_MOM_FP32> {
+    static constexpr int kRowBytes = kRowBytesF32, kTByte = kTByteF32, kTChunk = 14;
+    static __device__ __forceinline__ float *row(void *base, int32_t r)
+    {
+        return static_cast<float *>(base) + (size_t)r * kSlots;
+    }
+    static __device__ __forceinline__ Chunk load(const StepArgs &a, int32_t r, int c)
+    {
+        Chunk k;
+        k.m = ld4(row(a.m, r) + 4 * c);
+        k.v = ld4(row(a.v, r) + 4 * c);
+        k.t = __float_as_uint(k.m.w);           // slot 59 of m (meaningful for c == 14)
+        return k;
+    }
+    static __device__ __forceinline__ void store(const StepArgs &a, int32_t r, int c, Chunk k)
+    {
+        if (c == 14) k.m.w = __uint_as_float(k.t);
+        st4(row(a.m, r) + 4 * c, k.m);
+        st4(row(a.v, r) + 4 * c, k.v);
+    }
+};
+
+__device__ __forceinline__ float4 bf16x4_to_f4(uint32_t lo, uint32_t hi)
 {
-    return static_cast<float *>(base) + (size_t)r * kSlots;
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&lo));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&hi));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ uint32_t pack_bf16x2(float x, float y)
+{
+    const __nv_bfloat162 p = __floats2bfloat162_rn(x, y);
+    return *reinterpret_cast<const uint32_t *>(&p);
 }
 
-__device__ __forceinline__ void scale4(float4 &x, float s)
+// BF16 rows of 64 slots (128 B); chunk c = 8 B at byte 8c; t = uint32 at byte
+// 120, loaded and stored with chunk 14 as one 16-B access (slots 56-63).
+template <>
+struct State<GS_MOM_BF16> {
+    static constexpr int kRowBytes = kRowBytesBf16, kTByte = kTByteBf16, kTChunk = 14;
+    static __device__ __forceinline__ char *row(void *base, int32_t r)
+    {
+        return static_cast<char *>(base) + (size_t)r * kRowBytes;
+    }
+    static __device__ __forceinline__ Chunk load(const StepArgs &a, int32_t r, int c)
+    {
+        Chunk k;
+        if (c < 14) {
+            const uint2 um = *reinterpret_cast<const uint2 *>(row(a.m, r) + 8 * c);
+            k.m = bf16x4_to_f4(um.x, um.y);
+            k.t = 0;
+        } else {
+            const uint4 um = *reinterpret_cast<const uint4 *>(row(a.m, r) + 112);
+            k.m = bf16x4_to_f4(um.x, um.y);
+            k.t = um.z;
+        }
+        const uint2 uv = *reinterpret_cast<const uint2 *>(row(a.v, r) + 8 * c);
+        k.v = bf16x4_to_f4(uv.x, uv.y);
+        return k;
+    }
+    static __device__ __forceinline__ void store(const StepArgs &a, int32_t r, int c, const Chunk &k)
+    {
+        if (c < 14) {
+            __stcs(reinterpret_cast<uint2 *>(row(a.m, r) + 8 * c),
+                   make_uint2(pack_bf16x2(k.m.x, k.m.y), pack_bf16x2(k.m.z, k.m.w)));
+        } else {
+            __stcs(reinterpret_cast<uint4 *>(row(a.m, r) + 112),
+                   make_uint4(pack_bf16x2(k.m.x, k.m.y), pack_bf16x2(k.m.z, k.m.w), k.t, 0u));
+        }
+        __stcs(reinterpret_cast<uint2 *>(row(a.v, r) + 8 * c),
+               make_uint2(pack_bf16x2(k.v.x, k.v.y), pack_bf16x2(k.v.z, k.v.w)));
+    }
+};
+
+// MurmurHash3's 32-bit finaliser (Appleby, public domain): the random bits of
+// stochastic rounding, a function of (seed, iteration, row, slot) only.
+__device__ __forceinline__ uint32_t fmix32(uint32_t h)
 {
-    x.x *= s; x.y *= s; x.z *= s; x.w *= s;
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
 }
+
+// FP32 -> BF16 bits, rounded stochastically: add 16 random bits below the
+// kept mantissa and truncate (unbiased: rounds up with probability equal to
+// the discarded fraction).  Inf / NaN take the round-to-nearest path.
+__device__ __forceinline__ uint32_t bf16_bits_sr(float x, uint32_t rnd16)
+{
+    const uint32_t u = __float_as_uint(x);
+    if ((u & 0x7f800000u) == 0x7f800000u) return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+    return (u + (rnd16 & 0xffffu)) >> 16;
+}
+
+// BF16 hybrid: FP32 row of 16 slots (64 B) for SH DC, t, rotation, xyz,
+// scale, opacity; BF16 row of the 48 SH columns (96 B).  The 15 chunks map to:
+//   c = 0      DC0-2 (FP32 slots 0-2) + SH column 3 (BF16 slot 3); t = FP32 slot 3
+//   c = 1..11  SH columns 4c..4c+3 (BF16)
+//   c = 12..14 FP32 slots 4(c-11)..4(c-11)+3 (rotation; xyz + scale0; scale1-2 + opacity)
+// m is rounded to nearest; v stochastically (its ~0.1 % per-step EMA increment
+// is below BF16 resolution, and round-to-nearest would freeze it).
+template <>
+struct State<GS_MOM_BF16_HYBRID> {
+    static constexpr int kRowBytes = kRowBytesHyb, kTByte = kTByteHyb, kTChunk = 0;
+    static __device__ __forceinline__ float *frow(void *base, int32_t r)
+    {
+        return static_cast<float *>(base) + (size_t)r * 16;
+    }
+    static __device__ __forceinline__ char *shrow(void *base, int32_t r)
+    {
+        return static_cast<char *>(base) + (size_t)r * kRowBytesHybSh;
+    }
+    static __device__ __forceinline__ Chunk load(const StepArgs &a, int32_t r, int c)
+    {
+        Chunk k;
+        k.t = 0;
+        if (c >= 12) {
+            k.m = ld4(frow(a.m, r) + 4 * (c - 11));
+            k.v = ld4(frow(a.v, r) + 4 * (c - 11));
+        } else {
+            const uint2 um = *reinterpret_cast<const uint2 *>(shrow(a.m2, r) + 8 * c);
+            const uint2 uv = *reinterpret_cast<const uint2 *>(shrow(a.v2, r) + 8 * c);
+            k.m = bf16x4_to_f4(um.x, um.y);
+            k.v = bf16x4_to_f4(uv.x, uv.y);
+            if (c == 0) {
+                const float4 fm = ld4(frow(a.m, r)), fv = ld4(frow(a.v, r));
+                k.m.x = fm.x; k.m.y = fm.y; k.m.z = fm.z;
+                k.v.x = fv.x; k.v.y = fv.y; k.v.z = fv.z;
+                k.t = __float_as_uint(fm.w);
+            }
+        }
+        return k;
+    }
+    static __device__ __forceinline__ void store(const StepArgs &a, int32_t r, int c, const Chunk &k)
+    {
+        if (c >= 12) {
+            st4(frow(a.m, r) + 4 * (c - 11), k.m);
+            st4(frow(a.v, r) + 4 * (c - 11), k.v);
+            return;
+        }
+        const uint32_t h1 = fmix32((uint32_t)r * 0x9e3779b1u ^ (uint32_t)c * 0x85ebca77u ^
+                                   (uint32_t)a.k_ctr * 0xc2b2ae3du ^ (uint32_t)a.seed);
+        const uint32_t h2 = fmix32(h1 ^ 0x27d4eb2fu);
+        const uint32_t vlo = bf16_bits_sr(k.v.x, h1) | (bf16_bits_sr(k.v.y, h1 >> 16) << 16);
+        const uint32_t vhi = bf16_bits_sr(k.v.z, h2) | (bf16_bits_sr(k.v.w, h2 >> 16) << 16);
+        if (c == 0) {
+            st4(frow(a.m, r), make_float4(k.m.x, k.m.y, k.m.z, __uint_as_float(k.t)));
+            st4(frow(a.v, r), make_float4(k.v.x, k.v.y, k.v.z, 0.f));
+            // BF16 slots 0-2 are unused: only SH column 3 lives there
+            __stcs(reinterpret_cast<uint2 *>(shrow(a.m2, r)), make_uint2(0u, pack_bf16x2(0.f, k.m.w)));
+            __stcs(reinterpret_cast<uint2 *>(shrow(a.v2, r)), make_uint2(0u, vhi & 0xffff0000u));
+            return;
+        }
+        __stcs(reinterpret_cast<uint2 *>(shrow(a.m2, r) + 8 * c),
+               make_uint2(pack_bf16x2(k.m.x, k.m.y), pack_bf16x2(k.m.z, k.m.w)));
+        __stcs(reinterpret_cast<uint2 *>(shrow(a.v2, r) + 8 * c), make_uint2(vlo, vhi));
+    }
+};
+
+// ---------------------------------------------------------------- the items
 
 // One visible-row item: state chunk c (0..14) of `row` with its 4 attribute
 // columns; `sampled` applies the RSR post-scale; f = the row's bias factors.
+template <int kPrec>
 __device__ __forceinline__ void visible_item(const StepArgs &a, const int32_t row, const int c, const bool sampled,
                                              const float2 f)
 {
-    float *mr = state_row(a.m, row) + c * 4;
-    float *vr = state_row(a.v, row) + c * 4;
-    float4 m = ld4(mr), v = ld4(vr);
+    using S = State<kPrec>;
+    Chunk k = S::load(a, row, c);
+    float4 &m = k.m, &v = k.v;
+    const size_t r = (size_t)row;
     if (c < 12) {
         // 4 SH columns (column 4c .. 4c+3; 0-2 are the DC term)
-        const size_t off = (size_t)row * 48 + c * 4;
+        const size_t off = r * 48 + c * 4;
         float4 th = ld4(a.a_sh + off);
         const float4 g = ldg4_stream(a.g_sh + off);
         const float l0 = c == 0 ? a.lr[4] : a.lr[5], l3 = a.lr[5];
@@ -66,9 +233,9 @@ __device__ __forceinline__ void visible_item(const StepArgs &a, const int32_t ro
         st4(a.a_sh + off, th);
     } else if (c == 12) {
         // rotation quaternion
-        float *pt = a.a_rot + (size_t)row * 4;
+        float *pt = a.a_rot + r * 4;
         float4 th = ld4(pt);
-        const float4 g = ldg4_stream(a.g_rot + (size_t)row * 4);
+        const float4 g = ldg4_stream(a.g_rot + r * 4);
         const float l = a.lr[2];
         th.x = step_element(th.x, g.x, m.x, v.x, f.x, f.y, a, l, false, 0.f, 0.f, 0.f);
         th.y = step_element(th.y, g.y, m.y, v.y, f.x, f.y, a, l, false, 0.f, 0.f, 0.f);
@@ -77,10 +244,10 @@ __device__ __forceinline__ void visible_item(const StepArgs &a, const int32_t ro
         st4(pt, th);
     } else if (c == 13) {
         // xyz and the first log-scale component
-        float *px = a.a_xyz + (size_t)row * 3;
-        float *ps = a.a_scale + (size_t)row * 3;
-        const float *gx = a.g_xyz + (size_t)row * 3;
-        const float *gsp = a.g_scale + (size_t)row * 3;
+        float *px = a.a_xyz + r * 3;
+        float *ps = a.a_scale + r * 3;
+        const float *gx = a.g_xyz + r * 3;
+        const float *gsp = a.g_scale + r * 3;
         float x0 = px[0], x1 = px[1], x2 = px[2], s0 = ps[0];
         const float g0 = __ldcs(gx), g1 = __ldcs(gx + 1), g2 = __ldcs(gx + 2), gs0 = __ldcs(gsp);
         const bool ds = a.dar_s != 0;
@@ -94,12 +261,11 @@ __device__ __forceinline__ void visible_item(const StepArgs &a, const int32_t ro
         __stcs(ps, s0);
     } else {
         // the other two log-scale components, the opacity logit, t
-        float *ps = a.a_scale + (size_t)row * 3;
-        float *po = a.a_op + row;
-        const float *gsp = a.g_scale + (size_t)row * 3;
-        const float *gop = a.g_op + row;
+        float *ps = a.a_scale + r * 3;
+        float *po = a.a_op + r;
+        const float *gsp = a.g_scale + r * 3;
         float s1 = ps[1], s2 = ps[2], op = *po;
-        const float gs1 = __ldcs(gsp + 1), gs2 = __ldcs(gsp + 2), go = __ldcs(gop);
+        const float gs1 = __ldcs(gsp + 1), gs2 = __ldcs(gsp + 2), go = __ldcs(a.g_op + r);
         const bool ds = a.dar_s != 0, dop = a.dar_o != 0;
         const float r1s = ds ? expf(s1) : 0.f, r2s = ds ? expf(s2) : 0.f;
         // opacity: dR/dtau = sig'(tau) at the old value (App. Eq. opacity)
@@ -107,37 +273,31 @@ __device__ __forceinline__ void visible_item(const StepArgs &a, const int32_t ro
         s1 = step_element(s1, gs1, m.x, v.x, f.x, f.y, a, a.lr[1], ds, r1s, a.lam_s, a.clip_s);
         s2 = step_element(s2, gs2, m.y, v.y, f.x, f.y, a, a.lr[1], ds, r2s, a.lam_s, a.clip_s);
         op = step_element(op, go, m.z, v.z, f.x, f.y, a, a.lr[3], dop, rop, a.lam_o, a.clip_o);
-        m.w = __uint_as_float(__float_as_uint(m.w) + 1u);     // t += 1
         __stcs(ps + 1, s1); __stcs(ps + 2, s2);
         __stcs(po, op);
-        if (sampled) {     // RSR leaves t (m slot 59) and the unused v slot alone
-            m.x *= a.alpha1; m.y *= a.alpha1; m.z *= a.alpha1;
-            v.x *= a.alpha2; v.y *= a.alpha2; v.z *= a.alpha2;
-        }
-        st4(mr, m);
-        st4(vr, v);
-        return;
     }
-    if (sampled) {         // RSR post-scale of a sampled visible row
-        scale4(m, a.alpha1);
-        scale4(v, a.alpha2);
+    if (c == S::kTChunk) k.t += 1u;     // the row's own step count (Sec. 3.2)
+    if (sampled) {         // RSR post-scale of a sampled visible row (chunk 14 has 3 moments)
+        m.x *= a.alpha1; m.y *= a.alpha1; m.z *= a.alpha1;
+        v.x *= a.alpha2; v.y *= a.alpha2; v.z *= a.alpha2;
+        if (c != 14) { m.w *= a.alpha1; v.w *= a.alpha2; }
     }
-    st4(mr, m);
-    st4(vr, v);
+    S::store(a, row, c, k);
 }
 
-// RSR on state chunk c of an invisible StSS-sampled row (slot 59 of m is t).
+// RSR on state chunk c of an invisible StSS-sampled row (Eq. meth::restate).
+template <int kPrec>
 __device__ __forceinline__ void rsr_item(const StepArgs &a, const int32_t row, const int c)
 {
-    float *mr = state_row(a.m, row) + c * 4;
-    float *vr = state_row(a.v, row) + c * 4;
-    float4 m = ld4(mr), v = ld4(vr);
-    m.x *= a.alpha1; m.y *= a.alpha1; m.z *= a.alpha1;
-    v.x *= a.alpha2; v.y *= a.alpha2; v.z *= a.alpha2;
-    if (c != 14) { m.w *= a.alpha1; v.w *= a.alpha2; }
-    st4(mr, m);
-    st4(vr, v);
+    using S = State<kPrec>;
+    Chunk k = S::load(a, row, c);
+    k.m.x *= a.alpha1; k.m.y *= a.alpha1; k.m.z *= a.alpha1;
+    k.v.x *= a.alpha2; k.v.y *= a.alpha2; k.v.z *= a.alpha2;
+    if (c != 14) { k.m.w *= a.alpha1; k.v.w *= a.alpha2; }
+    S::store(a, row, c, k);
 }
+
+// ---------------------------------------------------------------- phase A
 
 // Shared-memory lists of one tile.
 template <int kTile>
@@ -148,10 +308,11 @@ struct TileLists {
     int32_t cnt[2][kTile / 32];
 };
 
-// Phase A: decide visibility and StSS membership for the tile's rows, prefetch
-// the step counters of visible rows, and compact both row sets into `L`.
-// Returns the visible count in nv and the invisible-sampled count in nr.
-template <int kTile>
+// Decide visibility and StSS membership for the tile's rows, prefetch the
+// step counters of visible rows (at byte kTByte of their m row), and compact
+// both row sets into `L`.  Returns the visible count in nv and the
+// invisible-sampled count in nr.
+template <int kTile, int kRowBytes, int kTByte>
 __device__ __forceinline__ void tile_decide(const StepArgs &a, const int vis_src, const int64_t r0, TileLists<kTile> &L,
                                             int &nv, int &nr)
 {
@@ -178,7 +339,8 @@ __device__ __forceinline__ void tile_decide(const StepArgs &a, const int vis_src
                 vis = true;
             }
             if (vis && !a.bias_mode)
-                t_old[j] = reinterpret_cast<const uint32_t *>(state_row(a.m, (int32_t)row))[kSlotT];
+                t_old[j] = *reinterpret_cast<const uint32_t *>(static_cast<const char *>(a.m) +
+                                                               (size_t)row * kRowBytes + kTByte);
             if (a.mask_out) a.mask_out[row] = vis ? 1 : 0;
             if (a.restate) smp = stss_sampled(a, (int32_t)row);
         }
@@ -221,17 +383,18 @@ __device__ __forceinline__ void tile_decide(const StepArgs &a, const int vis_src
     __syncthreads();
 }
 
-template <int kTile, int kMinBlocks>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) step_tile_f32(const StepArgs a, const int vis_src)
+// ---------------------------------------------------------------- the kernel
+
+template <int kTile, int kMinBlocks, int kPrec>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) step_tile(const StepArgs a, const int vis_src)
 {
     static_assert(kTile % kThreads == 0, "tile must be a multiple of the block");
+    using S = State<kPrec>;
     __shared__ TileLists<kTile> L;
     const int tid = threadIdx.x;
     const int64_t r0 = (int64_t)blockIdx.x * kTile;
     int nv, nr;
-    tile_decide<kTile>(a, vis_src, r0, L, nv, nr);
-    const int32_t *s_list = L.list, *s_rlist = L.rlist;
-    const float2 *s_fac = L.fac;
+    tile_decide<kTile, S::kRowBytes, S::kTByte>(a, vis_src, r0, L, nv, nr);
 
     // ---- B: flat work loop, items grouped by kind
     const int e_sh = 12 * nv, e_vis = 15 * nv, e_all = e_vis + 15 * nr;
@@ -246,12 +409,12 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) step_tile_f32(const Step
                 j = q % nv;
                 c = 12 + q / nv;
             }
-            const int32_t e = s_list[j];
-            visible_item(a, e & 0x7fffffff, c, e < 0, s_fac[j]);
+            const int32_t e = L.list[j];
+            visible_item<kPrec>(a, e & 0x7fffffff, c, e < 0, L.fac[j]);
         } else {
             const int q = w - e_vis;
             const int j = q / 15, c = q - j * 15;
-            rsr_item(a, s_rlist[j], c);
+            rsr_item<kPrec>(a, L.rlist[j], c);
         }
     }
 }
@@ -267,7 +430,13 @@ cudaError_t launch_step(const StepArgs &a, int prec, int vis_src, cudaStream_t s
     const unsigned grid = (unsigned)((a.n_rows + kStepTile - 1) / kStepTile);
     switch (prec) {
     case GS_MOM_FP32:
-        step_tile_f32<kStepTile, kStepMinBlocks><<<grid, kThreads, 0, s>>>(a, vis_src);
+        step_tile<kStepTile, kStepMinBlocks, GS_MOM_FP32><<<grid, kThreads, 0, s>>>(a, vis_src);
+        break;
+    case GS_MOM_BF16:
+        step_tile<kStepTile, kStepMinBlocks, GS_MOM_BF16><<<grid, kThreads, 0, s>>>(a, vis_src);
+        break;
+    case GS_MOM_BF16_HYBRID:
+        step_tile<kStepTile, kStepMinBlocks, GS_MOM_BF16_HYBRID><<<grid, kThreads, 0, s>>>(a, vis_src);
         break;
     default:
         return cudaErrorNotSupported;
