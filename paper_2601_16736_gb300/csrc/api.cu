@@ -21,10 +21,8 @@ struct gs_opt {
     int64_t n_rows = 0;
     int64_t capacity = 0;         // rows the current state buffers hold
     void *m = nullptr, *v = nullptr;
-    void *msh = nullptr, *vsh = nullptr;          // BF16 hybrid: BF16 SH rows
     int64_t capacity2 = 0;        // rows the spare (re-index target) buffers hold
     void *m2 = nullptr, *v2 = nullptr;
-    void *msh2 = nullptr, *vsh2 = nullptr;
     double *tab1 = nullptr, *tab2 = nullptr;
     float2 *fac = nullptr;
     int32_t tab_len = 0;
@@ -50,8 +48,6 @@ size_t state_row_bytes(int prec)
 {
     return prec == GS_MOM_FP32 ? gs::kRowBytesF32 : prec == GS_MOM_BF16 ? gs::kRowBytesBf16 : gs::kRowBytesHyb;
 }
-
-size_t second_row_bytes(int prec) { return prec == GS_MOM_BF16_HYBRID ? gs::kRowBytesHybSh : 0; }
 
 gs_status fail_cuda(gs_opt *o, cudaError_t e)
 {
@@ -170,28 +166,23 @@ int32_t table_length(double b1, double b2)
     return kMaxTable;
 }
 
-// Allocate the m, v rows (and the hybrid's BF16 SH rows) of `rows`
-// primitives; on failure everything allocated here is freed again.
-gs_status alloc_state(gs_opt *o, int64_t rows, void **m, void **v, void **m2, void **v2)
+// Allocate the m, v rows of `rows` primitives; on failure nothing stays
+// allocated.
+gs_status alloc_state(gs_opt *o, int64_t rows, void **m, void **v)
 {
-    const size_t n = (size_t)(rows > 0 ? rows : 1);
-    const size_t bytes = state_row_bytes(o->cfg.prec) * n, bytes2 = second_row_bytes(o->cfg.prec) * n;
-    *m = *v = *m2 = *v2 = nullptr;
-    bool ok = cudaMalloc(m, bytes) == cudaSuccess && cudaMalloc(v, bytes) == cudaSuccess;
-    if (ok && bytes2) ok = cudaMalloc(m2, bytes2) == cudaSuccess && cudaMalloc(v2, bytes2) == cudaSuccess;
-    if (!ok) {
+    const size_t bytes = state_row_bytes(o->cfg.prec) * (size_t)(rows > 0 ? rows : 1);
+    *m = *v = nullptr;
+    if (cudaMalloc(m, bytes) != cudaSuccess || cudaMalloc(v, bytes) != cudaSuccess) {
         cudaGetLastError();
-        cudaFree(*m); cudaFree(*v); cudaFree(*m2); cudaFree(*v2);
-        *m = *v = *m2 = *v2 = nullptr;
+        cudaFree(*m);
+        cudaFree(*v);
+        *m = *v = nullptr;
         return GS_ERR_OOM;
     }
     return GS_OK;
 }
 
-gs::StateView view(const gs_opt *o)
-{
-    return gs::StateView{o->cfg.prec, o->m, o->v, o->msh, o->vsh};
-}
+gs::StateView view(const gs_opt *o) { return gs::StateView{o->cfg.prec, o->m, o->v}; }
 
 bool params_ok(const gs_opt *o, const gs_step_params *p)
 {
@@ -209,8 +200,6 @@ void fill_args(const gs_opt *o, const gs_step_params *p, StepArgs *a)
     memset(a, 0, sizeof(*a));
     a->m = o->m;
     a->v = o->v;
-    a->m2 = o->msh;
-    a->v2 = o->vsh;
     a->fac = o->fac;
     a->fac_len = o->tab_len;
     a->n_rows = (int32_t)o->n_rows;
@@ -304,7 +293,7 @@ gs_status gs_opt_init(gs_opt **out, const gs_opt_config *cfg, int64_t n_rows, vo
     }
     o->n_rows = n_rows;
     o->capacity = n_rows > 0 ? n_rows : 1;
-    st = alloc_state(o, o->capacity, &o->m, &o->v, &o->msh, &o->vsh);
+    st = alloc_state(o, o->capacity, &o->m, &o->v);
     if (st != GS_OK) {
         gs_opt_destroy(o);
         return st;
@@ -320,8 +309,6 @@ gs_status gs_opt_init(gs_opt **out, const gs_opt_config *cfg, int64_t n_rows, vo
     }
     const size_t sbytes = state_row_bytes(c.prec) * (size_t)o->capacity;
     if ((e = cudaMemsetAsync(o->m, 0, sbytes, s)) != cudaSuccess || (e = cudaMemsetAsync(o->v, 0, sbytes, s)) != cudaSuccess ||
-        (o->msh && (e = cudaMemsetAsync(o->msh, 0, second_row_bytes(c.prec) * (size_t)o->capacity, s)) != cudaSuccess) ||
-        (o->vsh && (e = cudaMemsetAsync(o->vsh, 0, second_row_bytes(c.prec) * (size_t)o->capacity, s)) != cudaSuccess) ||
         (e = cudaMemsetAsync(o->err, 0, sizeof(int32_t), s)) != cudaSuccess ||
         (e = gs::launch_bias_table(c.beta1, c.beta2, o->tab_len, o->tab1, o->tab2, o->fac, s)) != cudaSuccess) {
         gs_opt_destroy(o);
@@ -342,10 +329,6 @@ void gs_opt_destroy(gs_opt *o)
     cudaFree(o->v);
     cudaFree(o->m2);
     cudaFree(o->v2);
-    cudaFree(o->msh);
-    cudaFree(o->vsh);
-    cudaFree(o->msh2);
-    cudaFree(o->vsh2);
     cudaFree(o->tab1);
     cudaFree(o->tab2);
     cudaFree(o->fac);
@@ -486,23 +469,18 @@ gs_status gs_reindex_state(gs_opt *o, const int32_t *src_rows, const uint8_t *re
         // cudaFree waits for
         cudaFree(o->m2);
         cudaFree(o->v2);
-        cudaFree(o->msh2);
-        cudaFree(o->vsh2);
         o->m2 = o->v2 = nullptr;
-        o->msh2 = o->vsh2 = nullptr;
         o->capacity2 = 0;
         const int64_t cap = n_new > 0 ? n_new : 1;
-        gs_status a = alloc_state(o, cap, &o->m2, &o->v2, &o->msh2, &o->vsh2);
+        gs_status a = alloc_state(o, cap, &o->m2, &o->v2);
         if (a != GS_OK) return a;
         o->capacity2 = cap;
     }
-    const gs::StateView out{o->cfg.prec, o->m2, o->v2, o->msh2, o->vsh2};
+    const gs::StateView out{o->cfg.prec, o->m2, o->v2};
     cudaError_t e = gs::launch_reindex(view(o), (int32_t)o->n_rows, out, (int32_t)n_new, src_rows, reset, o->err, s);
     if (e != cudaSuccess) return fail_cuda(o, e);
     std::swap(o->m, o->m2);
     std::swap(o->v, o->v2);
-    std::swap(o->msh, o->msh2);
-    std::swap(o->vsh, o->vsh2);
     const int64_t tc = o->capacity;
     o->capacity = o->capacity2;
     o->capacity2 = tc;

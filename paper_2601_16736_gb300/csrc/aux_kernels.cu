@@ -80,19 +80,17 @@ __global__ void bias_table_kernel(double beta1, double beta2, int32_t len, doubl
 }
 
 // ------------------------------------------------------------------ reindex
-// One thread per (output row, 16-B chunk of its state): kChunks1 chunks of the
-// m and v rows (FP32: slots 0-59 incl. the counter; BF16: the whole 128-B row
-// incl. the counter at byte 120; hybrid: the 64-B FP32 row incl. the counter)
-// and kChunks2 chunks of the hybrid's 96-B BF16 SH rows.  Copied from row
-// src[j], or zeroed for a fresh row.
-template <int kChunks1, int kRowBytes1, int kChunks2, int kRowBytes2>
+// One thread per (output row, 16-B chunk of its state rows): kChunks chunks
+// of the m and v rows (FP32: slots 0-59 incl. the counter; BF16: the whole
+// 128-B row incl. the counter at byte 120; hybrid: the whole 160-B row).
+// Copied from row src[j], or zeroed for a fresh row.
+template <int kChunks, int kRowBytes>
 __global__ void reindex_kernel(const StateView in, int32_t n_in, const StateView out, int32_t n_out,
                                const int32_t *__restrict__ src, const uint8_t *__restrict__ reset, int32_t *err)
 {
-    constexpr int kPer = kChunks1 + kChunks2;
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t j = gid / kPer;
-    const int c = (int)(gid - j * kPer);
+    const int64_t j = gid / kChunks;
+    const int c = (int)(gid - j * kChunks);
     if (j >= n_out) return;
     int32_t s = src[j];
     if (s >= n_in) {
@@ -100,30 +98,22 @@ __global__ void reindex_kernel(const StateView in, int32_t n_in, const StateView
         s = -1;
     }
     const bool fresh = s < 0 || (reset && reset[j]);
-    const bool first = c < kChunks1;
-    const int cc = first ? c : c - kChunks1;
-    const int rb = first ? kRowBytes1 : kRowBytes2;
-    const char *im = static_cast<const char *>(first ? in.m : in.m2);
-    const char *iv = static_cast<const char *>(first ? in.v : in.v2);
-    char *om = static_cast<char *>(first ? out.m : out.m2);
-    char *ov = static_cast<char *>(first ? out.v : out.v2);
     uint4 mv = make_uint4(0u, 0u, 0u, 0u), vv = mv;
     if (!fresh) {
-        mv = *reinterpret_cast<const uint4 *>(im + (size_t)s * rb + 16 * cc);
-        vv = *reinterpret_cast<const uint4 *>(iv + (size_t)s * rb + 16 * cc);
+        mv = *reinterpret_cast<const uint4 *>(static_cast<const char *>(in.m) + (size_t)s * kRowBytes + 16 * c);
+        vv = *reinterpret_cast<const uint4 *>(static_cast<const char *>(in.v) + (size_t)s * kRowBytes + 16 * c);
     }
-    *reinterpret_cast<uint4 *>(om + (size_t)j * rb + 16 * cc) = mv;
-    *reinterpret_cast<uint4 *>(ov + (size_t)j * rb + 16 * cc) = vv;
+    *reinterpret_cast<uint4 *>(static_cast<char *>(out.m) + (size_t)j * kRowBytes + 16 * c) = mv;
+    *reinterpret_cast<uint4 *>(static_cast<char *>(out.v) + (size_t)j * kRowBytes + 16 * c) = vv;
 }
 
 // ------------------------------------------------------------ export/import
 // Canonical layout: [n][59] FP32 in the column order xyz, scale, rot,
 // opacity, sh; one thread per (row, column).
 
-// Where column c of row r of one moment (rows base, second rows base2)
-// lives: a pointer to an FP32 value, or (through *bf) to a BF16 value.
-__device__ __forceinline__ float *locate(const StateView &st, void *base, void *base2, int64_t r, int c,
-                                         __nv_bfloat16 **bf)
+// Where column c of row r of one moment array lives: a pointer to an FP32
+// value, or (through *bf) to a BF16 value.
+__device__ __forceinline__ float *locate(const StateView &st, void *base, int64_t r, int c, __nv_bfloat16 **bf)
 {
     *bf = nullptr;
     if (st.prec == GS_MOM_FP32) return static_cast<float *>(base) + r * kSlots + slot_of_col(c);
@@ -131,14 +121,15 @@ __device__ __forceinline__ float *locate(const StateView &st, void *base, void *
         *bf = reinterpret_cast<__nv_bfloat16 *>(static_cast<char *>(base) + r * kRowBytesBf16) + slot_of_col(c);
         return nullptr;
     }
-    // hybrid FP32 row: [0-2] SH DC, [3] t, [4-7] rot, [8-10] xyz, [11-13] scale, [14] opacity
-    float *f = static_cast<float *>(base) + r * 16;
+    // hybrid FP32 part: [0-2] SH DC, [3] t, [4-7] rot, [8-10] xyz, [11-13] scale, [14] opacity
+    char *row = static_cast<char *>(base) + r * kRowBytesHyb;
+    float *f = reinterpret_cast<float *>(row);
     if (c < 3) return f + 8 + c;
     if (c < 6) return f + 11 + (c - 3);
     if (c < 10) return f + 4 + (c - 6);
     if (c == 10) return f + 14;
     if (c < 14) return f + (c - 11);
-    *bf = reinterpret_cast<__nv_bfloat16 *>(static_cast<char *>(base2) + r * kRowBytesHybSh) + (c - 11);
+    *bf = reinterpret_cast<__nv_bfloat16 *>(row + kHybShByte) + (c - 11);
     return nullptr;
 }
 
@@ -159,11 +150,11 @@ __global__ void export_kernel(const StateView st, int32_t n, float *__restrict__
     const int c = (int)(gid - r * kNumCols);
     __nv_bfloat16 *b;
     if (m_out) {
-        const float *p = locate(st, st.m, st.m2, r, c, &b);
+        const float *p = locate(st, st.m, r, c, &b);
         m_out[gid] = p ? *p : __bfloat162float(*b);
     }
     if (v_out) {
-        const float *p = locate(st, st.v, st.v2, r, c, &b);
+        const float *p = locate(st, st.v, r, c, &b);
         v_out[gid] = p ? *p : __bfloat162float(*b);
     }
     if (t_out && c == 0) t_out[r] = *t_of(st, r);
@@ -178,11 +169,11 @@ __global__ void import_kernel(const StateView st, int32_t n, const float *__rest
     const int c = (int)(gid - r * kNumCols);
     __nv_bfloat16 *b;
     if (m_in) {
-        float *p = locate(st, st.m, st.m2, r, c, &b);
+        float *p = locate(st, st.m, r, c, &b);
         if (p) *p = m_in[gid]; else *b = __float2bfloat16_rn(m_in[gid]);
     }
     if (v_in) {
-        float *p = locate(st, st.v, st.v2, r, c, &b);
+        float *p = locate(st, st.v, r, c, &b);
         if (p) *p = v_in[gid]; else *b = __float2bfloat16_rn(v_in[gid]);
     }
     if (t_in && c == 0) *t_of(st, r) = t_in[r];
@@ -241,16 +232,16 @@ cudaError_t launch_reindex(const StateView &in, int32_t n_in, const StateView &o
     if (n_out <= 0) return cudaSuccess;
     switch (in.prec) {
     case GS_MOM_FP32:
-        reindex_kernel<15, kRowBytesF32, 0, 16><<<blocks_for((int64_t)n_out * 15), kThreads, 0, s>>>(
-            in, n_in, out, n_out, src, reset, err);
+        reindex_kernel<15, kRowBytesF32><<<blocks_for((int64_t)n_out * 15), kThreads, 0, s>>>(in, n_in, out, n_out,
+                                                                                             src, reset, err);
         break;
     case GS_MOM_BF16:
-        reindex_kernel<8, kRowBytesBf16, 0, 16><<<blocks_for((int64_t)n_out * 8), kThreads, 0, s>>>(
-            in, n_in, out, n_out, src, reset, err);
+        reindex_kernel<8, kRowBytesBf16><<<blocks_for((int64_t)n_out * 8), kThreads, 0, s>>>(in, n_in, out, n_out,
+                                                                                            src, reset, err);
         break;
     case GS_MOM_BF16_HYBRID:
-        reindex_kernel<4, kRowBytesHyb, 6, kRowBytesHybSh><<<blocks_for((int64_t)n_out * 10), kThreads, 0, s>>>(
-            in, n_in, out, n_out, src, reset, err);
+        reindex_kernel<10, kRowBytesHyb><<<blocks_for((int64_t)n_out * 10), kThreads, 0, s>>>(in, n_in, out, n_out,
+                                                                                             src, reset, err);
         break;
     default:
         return cudaErrorNotSupported;

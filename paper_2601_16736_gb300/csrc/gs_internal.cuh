@@ -25,15 +25,16 @@ namespace gs {
 //   60-63 padding, never read
 // BF16 uses the same slots at 2 B each (128-B rows; slot 59 unused, t is one
 // uint32 at byte 120, i.e. slots 60-61).
-// The BF16 hybrid stores each moment in two rows: an FP32 row of 16 slots
-// (64 B) for the 14 columns whose learning rate is large relative to their
-// magnitude — [0-2] SH DC, [3] t (m only), [4-7] rotation, [8-10] xyz,
-// [11-13] scale, [14] opacity, [15] unused — and a BF16 row of the 48 SH
-// columns (96 B; slots 0-2 unused, the DC moments live in the FP32 row).
+// The BF16 hybrid row (160 B) has an FP32 part of 16 slots (bytes 0-63) for
+// the 14 columns whose learning rate is large relative to their magnitude —
+// [0-2] SH DC, [3] t (m only), [4-7] rotation, [8-10] xyz, [11-13] scale,
+// [14] opacity, [15] unused — followed by a BF16 part of the 48 SH columns
+// (bytes 64-159; its slots 0-2 are unused, the DC moments live in the FP32
+// part).
 constexpr int kSlots = 64;
 constexpr int kRowBytesF32 = 256, kTByteF32 = 4 * 59;
 constexpr int kRowBytesBf16 = 128, kTByteBf16 = 120;
-constexpr int kRowBytesHyb = 64, kTByteHyb = 12, kRowBytesHybSh = 96;
+constexpr int kRowBytesHyb = 160, kTByteHyb = 12, kHybShByte = 64;
 constexpr int kSlotSh = 0, kSlotRot = 48, kSlotXyz = 52, kSlotScale = 55, kSlotOpacity = 58;
 constexpr int kSlotT = 59;
 constexpr int kNumCols = 59;
@@ -56,7 +57,6 @@ struct StepArgs {
     float *a_xyz, *a_scale, *a_rot, *a_op, *a_sh;
     const float *g_xyz, *g_scale, *g_rot, *g_op, *g_sh;
     void *m, *v;                 // state rows
-    void *m2, *v2;               // BF16 hybrid: the BF16 SH rows (m, v above are its FP32 rows)
     const float2 *fac;           // per step count k: {1/(1-b1^k), 1/sqrt(1-b2^k)}
     int32_t fac_len;             // factors are exactly 1.0f from here on
     int32_t n_rows;
@@ -151,12 +151,10 @@ cudaError_t launch_visibility(const float *xyz, int32_t n, const float cam[16], 
                               int32_t *list, unsigned long long *count, cudaStream_t s);
 cudaError_t launch_bias_table(double beta1, double beta2, int32_t len, double *t1, double *t2,
                               float2 *fac, cudaStream_t s);
-// State of one context as the kernels see it: m, v rows and, for the BF16
-// hybrid, its BF16 SH rows m2, v2.
+// State of one context as the kernels see it: its format and m, v rows.
 struct StateView {
     int prec;
     void *m, *v;
-    void *m2, *v2;
 };
 
 cudaError_t launch_reindex(const StateView &in, int32_t n_in, const StateView &out, int32_t n_out,
