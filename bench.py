@@ -1,22 +1,27 @@
-"""Throughput of the fused AdamW-GS step (visibility + Sparse Adam + DAR + RSR)
-on the 1 M-primitive workload: 59 FP32 attributes per primitive (xyz 3,
-log-scale 3, quaternion 4, opacity logit 1, SH degree 3 48), means in 64
-Gaussian blobs, 200 ring/elevation views in random order (about 30 % of the
-primitives visible per view), DAR on opacity and scale every step, RSR every
-100 steps (StSS ratio 0.1), FP32 moments.
+"""Throughput of the fused AdamW-GS step (visibility + Sparse Adam + DAR + RSR).
 
-One step = one launch of the fused step kernel over all rows (frustum test +
-compaction + update of the visible rows; RSR rows on every 100th step).
+Headline (``value``): the 1 M-primitive workload — 59 FP32 attributes per
+primitive (xyz 3, log-scale 3, quaternion 4, opacity logit 1, SH degree 3 48),
+means in 64 Gaussian blobs, 200 ring/elevation views in random order (about
+30 % of the primitives visible per view), DAR on opacity and scale every step,
+RSR every 100 steps (StSS ratio 0.1), FP32 moments.  One step = one launch of
+the fused step kernel over all rows.
+
+``mixed_precision``: the 3 M-primitive workload (about 20 % visible) timed
+with FP32, BF16-hybrid and all-BF16 moments, each with its error against the
+FP64 oracle after 1000 steps on 2000 sampled primitives (group relative L2).
+
 Prints one JSON line.  Multi-GPU (torchrun): every rank runs an independent
-replica on its own scene (rows are independent; no data exchange), value =
-visible updates of all ranks / max time.
+replica on its own scene (rows are independent; no data exchange); value =
+visible updates of all ranks / the slowest rank's time.
 
---impl reference times the FP64 CPU oracle (the method's plain
-restatement) on a bounded sample of the same workload.
+--impl reference times the FP64 CPU oracle (the method's plain restatement)
+on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import subprocess
@@ -33,13 +38,18 @@ sys.path.insert(0, str(ROOT))
 METRIC = "visible Gaussians updated/s & HBM GB/s: mixed-prec vs FP32 step at ≤1e-3 err"
 UNIT = "visible Gaussians/s"
 WORKLOAD = "c2_1m"
-# algorithmic bytes (FP32 moments): per visible row theta, m, v read+write,
-# g read (59 values each) and t read+write; every row's 12-B mean is read once
-# for the frustum test (the visible rows' xyz read is that same read);
-# an invisible StSS-sampled row's m, v are read and written.
-BYTES_VISIBLE_F32 = 59 * 4 * 7 + 8 - 12
-BYTES_ROW_VIS = 12
-BYTES_RSR_F32 = 59 * 4 * 4
+MIXED_WORKLOAD = "c3_3m"
+# Algorithmic bytes per visible row: theta read + write and g read (59 FP32
+# values each), m and v read + write in the storage format, t read + write;
+# minus the row's 12-B mean, whose read is already counted by the frustum test.
+# FP32 moments 4 * 236 B; hybrid 4 * (45 * 2 + 14 * 4) B; BF16 4 * 59 * 2 B.
+STATE_RW = {"fp32": 4 * 236, "bf16_hybrid": 4 * (45 * 2 + 14 * 4), "bf16": 4 * 118}
+PREC_ENUM = {"fp32": 0, "bf16": 1, "bf16_hybrid": 3}
+BYTES_ROW_VIS = 12          # every row: the mean read by the frustum test
+
+
+def bytes_visible(prec: str) -> int:
+    return 3 * 236 + STATE_RW[prec] + 8 - 12
 
 
 def _peaks():
@@ -106,6 +116,137 @@ def _dist():
     return ws, rank, local
 
 
+class Scene:
+    """One workload resident on the GPU: attributes, a pool of gradient
+    buffers, cameras and the per-step parameters."""
+
+    def __init__(self, G, synth, wl, seed, total_steps):
+        import torch
+        self.G, self.synth, self.wl, self.seed = G, synth, wl, seed
+        groups = synth.scene_blobs(wl.n, seed, wl.extent) if wl.scene == "blobs" else synth.scene_uniform(wl.n, seed)
+        self.host_groups = groups
+        self.attrs0 = {k: torch.from_numpy(v).cuda() for k, v in groups.items()}
+        self.attrs = {k: v.clone() for k, v in self.attrs0.items()}
+        gen = torch.Generator(device="cuda").manual_seed(seed)
+        self.gbufs = []
+        for _ in range(wl.grad_buffers):
+            self.gbufs.append({name: torch.randn((wl.n, w), generator=gen, device="cuda", dtype=torch.float32)
+                               * (1e-4 if name == "xyz" else 1e-3) for name, w in synth.GROUPS})
+        self.cams = wl.cameras()
+        self.order = synth.view_order(len(self.cams), total_steps, seed)
+        self.total = total_steps
+        self.A = G.make_attrs(self.attrs)
+        self.GB = [G.make_attrs(g) for g in self.gbufs]
+        self.CAMS = [G.make_camera(c) for c in self.cams]
+        self.P = [self.params(k) for k in range(1, total_steps + 1)]
+
+    def params(self, k):
+        wl = self.wl
+        rs = k % wl.restate_every == 0
+        return self.G.make_params(self.synth.lr_for_step(k, self.total), k, dar_opacity=wl.dar, dar_scale=wl.dar,
+                                  restate=rs, restate_ratio=wl.restate_ratio, seed=self.seed)
+
+    def reset(self):
+        for k, v in self.attrs.items():
+            v.copy_(self.attrs0[k])
+
+
+def timed_run(G, sc, prec, steps, warmup, clocks_device=None, dist=None):
+    """Warm-up then `steps` timed launches of gs_step_camera on a fresh context;
+    CUDA events around the whole region and around every launch."""
+    import torch
+    L = G.lib()
+    sc.reset()
+    h = G.gs_opt_init(G.make_config(n_pixels=sc.wl.n_pixels, prec=PREC_ENUM[prec]), sc.wl.n)
+    counts = torch.zeros(warmup + steps, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+    sh = ctypes.c_void_p(stream.cuda_stream)
+    cnt = counts.data_ptr()
+
+    def launch(i):
+        s = L.gs_step_camera(h, ctypes.byref(sc.A), ctypes.byref(sc.GB[i % len(sc.GB)]),
+                             ctypes.byref(sc.CAMS[sc.order[i]]), None, ctypes.c_void_p(cnt + 8 * i),
+                             ctypes.byref(sc.P[i]), sh)
+        if s != 0:
+            raise G.GsError(s, "gs_step_camera")
+
+    for i in range(warmup):
+        launch(i)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(clocks_device) if clocks_device is not None else None
+    if dist is not None:
+        dist.barrier()
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for j in range(steps):
+        ev[j][0].record(stream)
+        launch(warmup + j)
+        ev[j][1].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    G.gs_opt_destroy(h)
+    elapsed = t0.elapsed_time(t1) / 1e3
+    kern = sum(a.elapsed_time(b) for a, b in ev) / 1e3 / steps
+    nv = counts.cpu().numpy()
+    timed_nv = int(nv[warmup:].sum())
+    rsr = 0
+    for j in range(steps):
+        k = warmup + 1 + j
+        if k % sc.wl.restate_every == 0:
+            rsr += int(round(sc.wl.restate_ratio * (sc.wl.n - int(nv[k - 1]))))
+    byt = (timed_nv * bytes_visible(prec) + steps * sc.wl.n * BYTES_ROW_VIS + rsr * STATE_RW[prec]) / steps
+    return dict(elapsed=elapsed, kern=kern, nv=timed_nv, bytes_per_launch=byt, clocks=clocks, steps=steps)
+
+
+def sampled_error(G, synth, orc, sc, prec, n_sample=2000, steps=1000):
+    """Group relative L2 error against the FP64 oracle after `steps` steps,
+    on `n_sample` primitives the oracle follows (their gradients drawn on the
+    host and written into the device buffers, so both sides see the same)."""
+    import torch
+    wl = sc.wl
+    sc.reset()
+    rng = np.random.default_rng(wl.seed + 77)
+    sample = np.sort(rng.choice(wl.n, n_sample, replace=False))
+    ids = torch.from_numpy(sample).cuda()
+    host_g = []
+    for b, gb in enumerate(sc.gbufs):
+        g = synth.grads_rows(n_sample, wl.seed + 1000 + b, 0)
+        host_g.append(g)
+        for name, sl in synth.GROUP_SLICES.items():
+            gb[name][ids] = torch.from_numpy(np.ascontiguousarray(g[:, sl])).cuda()
+    h = G.gs_opt_init(G.make_config(n_pixels=wl.n_pixels, prec=PREC_ENUM[prec]), wl.n)
+    mask = torch.zeros(wl.n, dtype=torch.uint8, device="cuda")
+    st = orc.State(synth.to_rows(sc.host_groups)[sample])
+    cfg = orc.Config(n_i=orc.dar_normaliser(wl.n_pixels))
+    diverged = np.zeros(n_sample, bool)
+    for k in range(1, steps + 1):
+        i = k - 1
+        cam = sc.cams[sc.order[i]]
+        p = sc.params(k)
+        G.gs_step_camera(h, sc.A, sc.GB[i % len(sc.GB)], sc.CAMS[sc.order[i]], p, mask_out=mask)
+        omask = orc.visibility_f32(st.theta[:, 0:3].astype(np.float32), cam)
+        diverged |= mask[ids].cpu().numpy() != omask
+        lr = synth.lr_for_step(k, sc.total)
+        orc.step(cfg, st, host_g[i % len(host_g)], omask, lr, wl.dar, wl.dar, k)
+        if k % wl.restate_every == 0:
+            orc.restate(cfg, st, sc.seed, k, wl.restate_ratio, row_ids=sample)
+    torch.cuda.synchronize()
+    G.gs_opt_destroy(h)
+    got = synth.to_rows({k: v[ids].cpu().numpy() for k, v in sc.attrs.items()})
+    keep = ~diverged
+    cols = {"xyz": slice(0, 3), "scale": slice(3, 6), "rot": slice(6, 10), "opacity": slice(10, 11),
+            "sh": slice(11, 59)}
+    errs = {g: float(np.linalg.norm(got[keep][:, s] - st.theta[keep][:, s]) /
+                     max(np.linalg.norm(st.theta[keep][:, s]), 1e-30)) for g, s in cols.items()}
+    return {"group_rel_l2": errs, "max": max(errs.values()), "rows": int(keep.sum()), "steps": steps}
+
+
 def run_ours(args):
     import torch
     from paper_2601_16736_gb300 import build as B
@@ -115,85 +256,16 @@ def run_ours(args):
 
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
+    dist = None
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     wl = synth.WORKLOADS[args.workload]
     seed = wl.seed + 1000 * rank
-    groups = synth.scene_blobs(wl.n, seed, wl.extent) if wl.scene == "blobs" else synth.scene_uniform(wl.n, seed)
-    cams = wl.cameras()
-    total_steps = args.warmup + args.steps
-    order = synth.view_order(len(cams), total_steps, seed)
-    attrs = {k: torch.from_numpy(v).cuda() for k, v in groups.items()}
-    # gradient buffers resident in HBM, one per step modulo the pool (drawn
-    # on the device: host generation of 8 x 59 M normals would dominate setup)
-    gen = torch.Generator(device="cuda").manual_seed(seed)
-    gbufs = []
-    for _ in range(wl.grad_buffers):
-        g = {}
-        for name, w in synth.GROUPS:
-            sig = 1e-4 if name == "xyz" else 1e-3
-            g[name] = torch.randn((wl.n, w), generator=gen, device="cuda", dtype=torch.float32) * sig
-        gbufs.append(g)
-    cfg = G.make_config(n_pixels=wl.n_pixels)
-    h = G.gs_opt_init(cfg, wl.n)
-    A = G.make_attrs(attrs)
-    GB = [G.make_attrs(g) for g in gbufs]
-    CAMS = [G.make_camera(c) for c in cams]
-    counts = torch.zeros(total_steps, dtype=torch.int64, device="cuda")
-    rsr_rows = 0
-    stream = torch.cuda.current_stream()
-
-    def params(k):
-        rs = k % wl.restate_every == 0
-        return G.make_params(synth.lr_for_step(k, total_steps), k, dar_opacity=wl.dar, dar_scale=wl.dar,
-                             restate=rs, restate_ratio=wl.restate_ratio, seed=seed)
-
-    P = [params(k) for k in range(1, total_steps + 1)]
-    cnt_ptr = counts.data_ptr()
-    import ctypes
-    L = G.lib()
-    sh = ctypes.c_void_p(stream.cuda_stream)
-
-    def launch(k):   # k is 1-based
-        i = k - 1
-        s = L.gs_step_camera(h, ctypes.byref(A), ctypes.byref(GB[i % len(GB)]), ctypes.byref(CAMS[order[i]]), None,
-                             ctypes.c_void_p(cnt_ptr + 8 * i), ctypes.byref(P[i]), sh)
-        if s != 0:
-            raise G.GsError(s, "gs_step_camera")
-
-    for k in range(1, args.warmup + 1):
-        launch(k)
-    torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    sampler = ClockSampler(local)
-    if ws > 1:
-        torch.distributed.barrier()
-    sampler.start()
-    time.sleep(0.3)
-    torch.cuda.synchronize()
-    t0.record(stream)
-    for j in range(args.steps):
-        k = args.warmup + 1 + j
-        ev[j][0].record(stream)
-        launch(k)
-        ev[j][1].record(stream)
-    t1.record(stream)
-    torch.cuda.synchronize()
-    clocks = sampler.stop()
-    elapsed = t0.elapsed_time(t1) / 1e3
-    kern = sum(a.elapsed_time(b) for a, b in ev) / 1e3 / args.steps
-    nv = counts.cpu().numpy()
-    timed_nv = int(nv[args.warmup:].sum())
-    # invisible StSS-sampled rows on the timed RSR steps (for the byte count)
-    from_rsr = 0
-    for j in range(args.steps):
-        k = args.warmup + 1 + j
-        if k % wl.restate_every == 0:
-            from_rsr += int(round(wl.restate_ratio * (wl.n - int(nv[k - 1]))))
-    if ws > 1:
-        import torch.distributed as dist
+    sc = Scene(G, synth, wl, seed, args.warmup + args.steps)
+    r = timed_run(G, sc, args.prec, args.steps, args.warmup, clocks_device=local, dist=dist)
+    elapsed, timed_nv = r["elapsed"], r["nv"]
+    if dist is not None:
         t = torch.tensor([elapsed, float(timed_nv)], dtype=torch.float64, device="cuda")
         tmax = t.clone()
         dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
@@ -202,52 +274,139 @@ def run_ours(args):
     else:
         elapsed_all, nv_all = elapsed, float(timed_nv)
 
-    # ---- end to end through the public C ABI with host gradients
-    e2e = None
-    if rank == 0 and args.e2e_steps > 0:
-        gh = [{k: v.cpu().pin_memory() for k, v in g.items()} for g in gbufs[:2]]
-        GH = [G.make_attrs(g) for g in gh]
-        h2d = sum(v.numel() * 4 for v in gh[0].values())
-        G.gs_step_host(h, A, GH[0], CAMS[0], P[0])
-        torch.cuda.synchronize()
-        tt = time.perf_counter()
-        tot = 0
-        for j in range(args.e2e_steps):
-            tot += G.gs_step_host(h, A, GH[j % 2], CAMS[order[j]], P[j])
-        dt = time.perf_counter() - tt
-        e2e = {"value": tot / dt, "unit": UNIT, "h2d_bytes_per_step": h2d + 64, "d2h_bytes_per_step": 8,
-               "steps": args.e2e_steps}
-    G.gs_opt_destroy(h)
-
-    value = nv_all / elapsed_all
-    mean_nv = timed_nv / args.steps
-    bytes_per_launch = (timed_nv * BYTES_VISIBLE_F32 + args.steps * wl.n * BYTES_ROW_VIS
-                        + from_rsr * BYTES_RSR_F32) / args.steps
     peak, peak_kind = _peaks()
-    achieved = bytes_per_launch / kern / 1e9
+    achieved = r["bytes_per_launch"] / r["kern"] / 1e9
     out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": elapsed_all / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "metric": METRIC, "value": nv_all / elapsed_all, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_all / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"{wl.name}: {wl.n} Gaussians, SH3 (59 fp32 attrs), 64 blobs, 200 views, "
-                               f"DAR+RSR(0.1/100), fp32 moments, fused visibility+step",
-                   "n_rows": wl.n, "visible_fraction": mean_nv / wl.n, "moments": "fp32",
+                               f"DAR+RSR(0.1/100), {args.prec} moments, fused visibility+step",
+                   "n_rows": wl.n, "visible_fraction": timed_nv / args.steps / wl.n, "moments": args.prec,
                    "l2": "inputs larger than L2: 0.94 GB of attributes/grads/state, ~0.5 GB touched per step",
                    "parallelism": f"replicas x{ws}"},
         "hbm_gbs": achieved,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_source": peak_kind, "traffic": args.traffic,
-                     "bytes_per_launch": bytes_per_launch, "kernel_ms": kern * 1e3},
+                     "bytes_per_launch": r["bytes_per_launch"], "kernel_ms": r["kern"] * 1e3},
         "gpu_launches": args.steps,
-        "clocks": clocks,
-        "e2e": e2e,
+        "clocks": r["clocks"],
     }
+
+    if rank == 0 and args.e2e_steps > 0:
+        gh = [{k: v.cpu().pin_memory() for k, v in g.items()} for g in sc.gbufs[:2]]
+        GH = [G.make_attrs(g) for g in gh]
+        h2d = sum(v.numel() * 4 for v in gh[0].values())
+        h = G.gs_opt_init(G.make_config(n_pixels=wl.n_pixels, prec=PREC_ENUM[args.prec]), wl.n)
+        G.gs_step_host(h, sc.A, GH[0], sc.CAMS[0], sc.P[0])
+        torch.cuda.synchronize()
+        tt = time.perf_counter()
+        tot = 0
+        for j in range(args.e2e_steps):
+            tot += G.gs_step_host(h, sc.A, GH[j % 2], sc.CAMS[sc.order[j]], sc.P[j])
+        dt = time.perf_counter() - tt
+        G.gs_opt_destroy(h)
+        out["e2e"] = {"value": tot / dt, "unit": UNIT, "h2d_bytes_per_step": h2d + 64, "d2h_bytes_per_step": 8,
+                      "steps": args.e2e_steps, "path": "gs_step_host: pinned host gradients H2D, step, count D2H"}
+    del sc
+    torch.cuda.empty_cache()
+
+    if rank == 0 and args.mixed:
+        import oracle
+        oracle.build()
+        mwl = synth.WORKLOADS[MIXED_WORKLOAD]
+        msc = Scene(G, synth, mwl, mwl.seed, max(1000, args.mixed_steps + 10))
+        legs = {}
+        for prec in ("fp32", "bf16_hybrid", "bf16"):
+            rr = timed_run(G, msc, prec, args.mixed_steps, 10)
+            legs[prec] = {"value": rr["nv"] / rr["elapsed"], "hbm_gbs": rr["bytes_per_launch"] / rr["kern"] / 1e9,
+                          "ms_per_step": rr["elapsed"] / args.mixed_steps * 1e3,
+                          "bytes_per_launch": rr["bytes_per_launch"]}
+            if args.mixed_error:
+                legs[prec]["error_vs_fp64_oracle"] = sampled_error(G, synth, oracle, msc, prec)
+        for prec in ("bf16_hybrid", "bf16"):
+            legs[prec]["speedup_vs_fp32"] = legs[prec]["value"] / legs["fp32"]["value"]
+        out["mixed_precision"] = {"workload": f"{mwl.name}: {mwl.n} Gaussians, ~20% visible, {args.mixed_steps} "
+                                              f"timed steps per format", "gate": "group relative L2 <= 1e-3",
+                                  **legs}
+    if rank == 0 and args.batched:
+        out["batched"] = batched_leg(G, synth, args.batched_steps)
     if rank == 0 and args.cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if rank == 0:
         print(json.dumps(out))
-    if ws > 1:
-        torch.distributed.destroy_process_group()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def batched_leg(G, synth, steps, n_scenes=16, seed=1004):
+    """16 independent scenes, primitive counts log-uniform in [50k, 2M] and
+    blob extents log-uniform in [6, 75] (10-60 % visible), each with its own
+    camera sequence and step counters: 16 separate FP32 launches per step vs
+    one batched persistent launch (eager, and replayed as a CUDA graph)."""
+    import torch
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(np.log(50_000), np.log(2_000_000), n_scenes)).astype(int)
+    extents = np.exp(rng.uniform(np.log(6.0), np.log(75.0), n_scenes))
+    scenes = []
+    for s in range(n_scenes):
+        groups = synth.scene_blobs(int(sizes[s]), seed + s, float(extents[s]))
+        attrs = {k: torch.from_numpy(v).cuda() for k, v in groups.items()}
+        gen = torch.Generator(device="cuda").manual_seed(seed + s)
+        grads = {n: torch.randn((int(sizes[s]), w), generator=gen, device="cuda") * (1e-4 if n == "xyz" else 1e-3)
+                 for n, w in synth.GROUPS}
+        cams = synth.ring_cameras(40, (-30.0, -15.0, 0.0, 15.0, 30.0))
+        order = synth.view_order(len(cams), 10_000, seed + s)
+        scenes.append(dict(n=int(sizes[s]), attrs=attrs, grads=grads, A=G.make_attrs(attrs), GR=G.make_attrs(grads),
+                           cams=[G.make_camera(c) for c in cams], order=order))
+    total = int(sizes.sum())
+
+    def params(k, s):
+        return G.make_params(synth.lr_for_step(k, 10_000), k, restate=(k % 100 == 0), restate_ratio=0.1, seed=s)
+
+    def timed(fn, nsteps, k0):
+        counts = torch.zeros(n_scenes, dtype=torch.int64, device="cuda")
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for j in range(nsteps):
+            fn(k0 + j, counts)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3, int(counts.sum().item())
+
+    res = {"workload": f"{n_scenes} scenes, {total} Gaussians in total (sizes log-uniform 50k-2M), FP32 moments",
+           "sizes": sizes.tolist()}
+    # 16 separate launches per step
+    hs = [G.gs_opt_init(G.make_config(), sc["n"]) for sc in scenes]
+
+    def sep(k, counts):
+        for s, sc in enumerate(scenes):
+            G.gs_step_camera(hs[s], sc["A"], sc["GR"], sc["cams"][sc["order"][k]], params(k, s),
+                             n_visible=counts[s:s + 1])
+    timed(sep, 5, 1)
+    dt, nv = timed(sep, steps, 6)
+    res["separate_launches"] = {"value": nv / dt, "ms_per_step": dt / steps * 1e3, "launches_per_step": n_scenes}
+    # one batched launch per step (tuning happens over the first calls)
+    b = G.gs_batch_create(hs)
+
+    def bat(k, counts, graph=False):
+        for s, sc in enumerate(scenes):
+            b.set(s, sc["A"], sc["GR"], sc["cams"][sc["order"][k]], params(k, s))
+        G.gs_batch_step(b, counts, graph=graph)
+    timed(bat, 3 * 4 + 4, 1000)
+    dt, nv = timed(bat, steps, 2000)
+    res["batched_persistent"] = {"value": nv / dt, "ms_per_step": dt / steps * 1e3, "launches_per_step": 1,
+                                 "tuned": G.gs_batch_config(b)}
+    timed(lambda k, c: bat(k, c, True), 3, 3000)
+    dt, nv = timed(lambda k, c: bat(k, c, True), steps, 4000)
+    res["batched_graph"] = {"value": nv / dt, "ms_per_step": dt / steps * 1e3, "launches_per_step": 1}
+    res["speedup_batched_vs_separate"] = res["batched_persistent"]["value"] / res["separate_launches"]["value"]
+    res["speedup_graph_vs_separate"] = res["batched_graph"]["value"] / res["separate_launches"]["value"]
+    b.close()
+    for h in hs:
+        G.gs_opt_destroy(h)
+    return res
 
 
 class OracleSample:
@@ -330,9 +489,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--prec", choices=list(PREC_ENUM), default="fp32")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-mixed", dest="mixed", action="store_false")
+    ap.add_argument("--mixed-steps", type=int, default=300)
+    ap.add_argument("--no-mixed-error", dest="mixed_error", action="store_false")
+    ap.add_argument("--no-batched", dest="batched", action="store_false")
+    ap.add_argument("--batched-steps", type=int, default=100)
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the step kernel for this workload (from profiles/)")
     args = ap.parse_args()

@@ -229,6 +229,56 @@ gs_status gs_step_host(gs_opt *opt, const gs_attrs *attrs, const gs_grads *grads
                        const gs_camera *cam, const gs_step_params *params,
                        int64_t *n_visible_host, void *stream);
 
+/*
+ * Batched step: several independent scenes (one context each, all with the
+ * same moment precision, on the same device) updated by ONE persistent launch
+ * whose CTAs pull (scene, tile) work items from a shared counter, so scenes
+ * of very different sizes keep every SM busy until the whole batch is done.
+ * Each scene has its own camera, parameters and step counters; the result of
+ * every scene is identical to gs_step_camera on that scene alone.
+ */
+#define GS_MAX_BATCH 64
+typedef struct gs_batch gs_batch;   /* opaque */
+
+/* Create a batch over n_scenes (1..GS_MAX_BATCH) existing contexts (not
+ * owned: they must outlive the batch).  Allocates a device scene table, two
+ * pinned staging buffers and the work counters. */
+gs_status gs_batch_create(gs_batch **out, gs_opt *const *scenes, int32_t n_scenes);
+
+/* Free the batch (synchronises the device); NULL is ignored. */
+void gs_batch_destroy(gs_batch *b);
+
+/*
+ * One step of every scene: scene s uses attrs[s], grads[s], cams[s],
+ * params[s] (host arrays of n_scenes entries; the pointers inside are device
+ * memory, validated as for gs_step_camera).  n_visible: optional device
+ * int64[n_scenes]; each scene's visible count is added to its entry.
+ * The scene table is staged in pinned memory and copied to the device on
+ * `stream` before the launch.  Autotuning: the first calls of a batch run
+ * each candidate launch configuration (rows per tile, SH columns per work
+ * item, CTAs per SM) in turn — 3 times each — and time them with CUDA events;
+ * afterwards the fastest is used.  All candidates compute identical results,
+ * so tuning happens on real steps.
+ */
+gs_status gs_batch_step(gs_batch *b, const gs_attrs *attrs, const gs_grads *grads, const gs_camera *cams,
+                        const gs_step_params *params, int64_t *n_visible, void *stream);
+
+/*
+ * gs_batch_step through a CUDA graph that the batch builds itself (a copy
+ * node for the scene table and the kernel node) once tuning has finished;
+ * each call refreshes the copy node's source (alternating between the two
+ * pinned buffers) and launches the graph.  Before tuning has finished it
+ * behaves as gs_batch_step.
+ */
+gs_status gs_batch_graph_step(gs_batch *b, const gs_attrs *attrs, const gs_grads *grads, const gs_camera *cams,
+                              const gs_step_params *params, int64_t *n_visible, void *stream);
+
+/* The launch configuration in use: rows per tile, SH columns per work item,
+ * CTAs per SM, and whether tuning has finished (1) or not (0).  Any output
+ * may be NULL. */
+gs_status gs_batch_config(const gs_batch *b, int32_t *tile_rows, int32_t *sh_width, int32_t *blocks_per_sm,
+                          int32_t *tuned);
+
 /* Largest primitive count gs_step_host_noalloc accepts. */
 #define GS_NOALLOC_MAX_ROWS 65536
 

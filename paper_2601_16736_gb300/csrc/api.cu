@@ -7,9 +7,12 @@
 #include <math.h>
 #include <string.h>
 
+#include <stddef.h>
+
 #include <algorithm>
 #include <atomic>
 #include <new>
+#include <vector>
 
 #include "gs_internal.cuh"
 
@@ -551,6 +554,259 @@ gs_status gs_opt_sync_errors(gs_opt *o, void *stream)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched step (gs_batch_*).
+
+struct gs_batch {
+    std::vector<gs_opt *> scenes;
+    int prec = 0;
+    int device = -1;
+    gs::BatchParams *d_params = nullptr;   // device scene table
+    unsigned *d_counters = nullptr;        // work, done
+    gs::BatchParams *h_slot[2] = {nullptr, nullptr};   // pinned staging
+    cudaEvent_t slot_ev[2] = {nullptr, nullptr};
+    bool slot_pending[2] = {false, false};
+    int next_slot = 0;
+    // autotuning
+    static constexpr int kReps = 3;
+    int n_cand = 0, best = -1, calls = 0;
+    std::vector<cudaEvent_t> ev;           // start / stop per tuning call
+    // graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t copy_node = nullptr;
+    size_t graph_bytes = 0;
+};
+
+namespace {
+
+size_t batch_bytes(int n) { return offsetof(gs::BatchParams, args) + (size_t)n * sizeof(StepArgs); }
+
+gs_status batch_check(gs_batch *b, const gs_attrs *attrs, const gs_grads *grads, const gs_camera *cams,
+                      const gs_step_params *params, int64_t *n_visible)
+{
+    if (!b || !attrs || !grads || !cams || !params) return GS_ERR_INVALID_ARG;
+    const int n = (int)b->scenes.size();
+    for (int s = 0; s < n; ++s) {
+        gs_opt *o = b->scenes[s];
+        gs_status st = precheck(o);
+        if (st != GS_OK) return st;
+        if (!camera_ok(&cams[s]) || !params_ok(o, &params[s])) return GS_ERR_INVALID_ARG;
+        if (!attrs_ok(o, attrs[s], o->n_rows) || !attrs_ok(o, grads[s], o->n_rows)) return GS_ERR_INVALID_ARG;
+    }
+    if (!dev_ok(b->scenes[0], n_visible, n_visible ? 8 * (size_t)n : 0, 8)) return GS_ERR_INVALID_ARG;
+    return GS_OK;
+}
+
+// Fill the scene table for candidate `cand` into host memory `hp`.
+void batch_fill(gs_batch *b, int cand, const gs_attrs *attrs, const gs_grads *grads, const gs_camera *cams,
+                const gs_step_params *params, int64_t *n_visible, gs::BatchParams *hp)
+{
+    int tile = 0, width = 0, mb = 0;
+    gs::batch_candidate_info(b->prec, cand, &tile, &width, &mb);
+    const int n = (int)b->scenes.size();
+    int total = 0;
+    for (int s = 0; s < n; ++s) {
+        const gs_opt *o = b->scenes[s];
+        hp->tile_start[s] = total;
+        total += (int)((o->n_rows + tile - 1) / tile);
+        StepArgs &a = hp->args[s];
+        fill_args(o, &params[s], &a);
+        set_attrs(&a, &attrs[s], &grads[s]);
+        memcpy(a.cam, &cams[s], sizeof(a.cam));
+        a.n_visible = n_visible ? reinterpret_cast<unsigned long long *>(n_visible + s) : nullptr;
+    }
+    hp->tile_start[n] = total;
+    hp->n_scenes = n;
+    hp->total_tiles = total;
+}
+
+// Take the next pinned slot (waiting until the copy that last read it ran).
+cudaError_t batch_slot(gs_batch *b, int *slot)
+{
+    const int k = b->next_slot;
+    b->next_slot ^= 1;
+    if (b->slot_pending[k]) {
+        const cudaError_t e = cudaEventSynchronize(b->slot_ev[k]);
+        if (e != cudaSuccess) return e;
+        b->slot_pending[k] = false;
+    }
+    *slot = k;
+    return cudaSuccess;
+}
+
+// Candidate for this call: the tuning schedule, then the fastest.
+cudaError_t batch_pick(gs_batch *b, int *cand, bool *timed)
+{
+    *timed = false;
+    if (b->best >= 0) {
+        *cand = b->best;
+        return cudaSuccess;
+    }
+    const int total = b->n_cand * gs_batch::kReps;
+    if (b->calls < total) {
+        *cand = b->calls % b->n_cand;
+        *timed = true;
+        return cudaSuccess;
+    }
+    // all timings issued: read them and keep the fastest candidate
+    cudaError_t e = cudaEventSynchronize(b->ev[2 * total - 1]);
+    if (e != cudaSuccess) return e;
+    std::vector<float> sum(b->n_cand, 0.f);
+    for (int c = 0; c < total; ++c) {
+        float ms = 0.f;
+        if ((e = cudaEventElapsedTime(&ms, b->ev[2 * c], b->ev[2 * c + 1])) != cudaSuccess) return e;
+        sum[c % b->n_cand] += ms;
+    }
+    b->best = (int)(std::min_element(sum.begin(), sum.end()) - sum.begin());
+    *cand = b->best;
+    return cudaSuccess;
+}
+
+gs_status batch_run(gs_batch *b, const gs_attrs *attrs, const gs_grads *grads, const gs_camera *cams,
+                    const gs_step_params *params, int64_t *n_visible, void *stream, bool graph)
+{
+    gs_status st = batch_check(b, attrs, grads, cams, params, n_visible);
+    if (st != GS_OK) return st;
+    gs_opt *o0 = b->scenes[0];
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int cand = 0, slot = 0;
+    bool timed = false;
+    cudaError_t e = batch_pick(b, &cand, &timed);
+    if (e == cudaSuccess) e = batch_slot(b, &slot);
+    if (e != cudaSuccess) return fail_cuda(o0, e);
+    batch_fill(b, cand, attrs, grads, cams, params, n_visible, b->h_slot[slot]);
+    const size_t bytes = batch_bytes((int)b->scenes.size());
+    if (graph && b->best >= 0) {
+        if (!b->exec) {
+            int grid = 0;
+            void *fn = nullptr;
+            if ((e = gs::launch_batch(b->d_params, b->d_counters, b->d_counters + 1, b->prec, cand, s, &grid, &fn)) !=
+                cudaSuccess)
+                return fail_cuda(o0, e);
+            cudaGraphNode_t kern = nullptr;
+            cudaKernelNodeParams kp = {};
+            unsigned *work = b->d_counters, *done = b->d_counters + 1;
+            void *args[3] = {&b->d_params, &work, &done};
+            kp.func = fn;
+            kp.gridDim = dim3((unsigned)grid);
+            kp.blockDim = dim3(256);
+            kp.kernelParams = args;
+            if ((e = cudaGraphCreate(&b->graph, 0)) != cudaSuccess ||
+                (e = cudaGraphAddMemcpyNode1D(&b->copy_node, b->graph, nullptr, 0, b->d_params, b->h_slot[slot], bytes,
+                                              cudaMemcpyHostToDevice)) != cudaSuccess ||
+                (e = cudaGraphAddKernelNode(&kern, b->graph, &b->copy_node, 1, &kp)) != cudaSuccess ||
+                (e = cudaGraphInstantiate(&b->exec, b->graph, 0)) != cudaSuccess)
+                return fail_cuda(o0, e);
+            b->graph_bytes = bytes;
+        } else if ((e = cudaGraphExecMemcpyNodeSetParams1D(b->exec, b->copy_node, b->d_params, b->h_slot[slot], bytes,
+                                                             cudaMemcpyHostToDevice)) != cudaSuccess) {
+            return fail_cuda(o0, e);
+        }
+        e = cudaGraphLaunch(b->exec, s);
+        if (e == cudaSuccess) e = cudaEventRecord(b->slot_ev[slot], s);
+        if (e != cudaSuccess) return fail_cuda(o0, e);
+        b->slot_pending[slot] = true;
+        return GS_OK;
+    }
+    e = cudaMemcpyAsync(b->d_params, b->h_slot[slot], bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaEventRecord(b->slot_ev[slot], s);
+    if (e != cudaSuccess) return fail_cuda(o0, e);
+    b->slot_pending[slot] = true;
+    if (timed) e = cudaEventRecord(b->ev[2 * b->calls], s);
+    if (e == cudaSuccess)
+        e = gs::launch_batch(b->d_params, b->d_counters, b->d_counters + 1, b->prec, cand, s, nullptr, nullptr);
+    if (e == cudaSuccess && timed) e = cudaEventRecord(b->ev[2 * b->calls + 1], s);
+    if (e != cudaSuccess) return fail_cuda(o0, e);
+    if (timed) ++b->calls;
+    return GS_OK;
+}
+
+}  // namespace
+
+extern "C" gs_status gs_batch_create(gs_batch **out, gs_opt *const *scenes, int32_t n_scenes)
+{
+    if (!out) return GS_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!scenes || n_scenes < 1 || n_scenes > GS_MAX_BATCH) return GS_ERR_INVALID_ARG;
+    for (int s = 0; s < n_scenes; ++s) {
+        gs_status st = precheck(scenes[s]);
+        if (st != GS_OK) return st;
+        if (scenes[s]->cfg.prec != scenes[0]->cfg.prec || scenes[s]->device != scenes[0]->device)
+            return GS_ERR_INVALID_ARG;
+    }
+    gs_batch *b = new (std::nothrow) gs_batch;
+    if (!b) return GS_ERR_OOM;
+    b->scenes.assign(scenes, scenes + n_scenes);
+    b->prec = scenes[0]->cfg.prec;
+    b->device = scenes[0]->device;
+    b->n_cand = gs::batch_candidates(b->prec);
+    const size_t bytes = sizeof(gs::BatchParams);
+    bool ok = b->n_cand > 0 && cudaMalloc(&b->d_params, bytes) == cudaSuccess &&
+              cudaMalloc(&b->d_counters, 2 * sizeof(unsigned)) == cudaSuccess &&
+              cudaMemset(b->d_counters, 0, 2 * sizeof(unsigned)) == cudaSuccess &&
+              cudaMallocHost(&b->h_slot[0], bytes) == cudaSuccess && cudaMallocHost(&b->h_slot[1], bytes) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->slot_ev[0], cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->slot_ev[1], cudaEventDisableTiming) == cudaSuccess;
+    if (ok) {
+        b->ev.resize(2 * b->n_cand * gs_batch::kReps, nullptr);
+        for (auto &e : b->ev) ok = ok && cudaEventCreate(&e) == cudaSuccess;
+    }
+    if (!ok) {
+        cudaGetLastError();
+        const gs_status st = b->n_cand > 0 ? GS_ERR_OOM : GS_ERR_UNSUPPORTED;
+        gs_batch_destroy(b);
+        return st;
+    }
+    *out = b;
+    return GS_OK;
+}
+
+extern "C" void gs_batch_destroy(gs_batch *b)
+{
+    if (!b) return;
+    if (b->device >= 0) cudaSetDevice(b->device);
+    cudaDeviceSynchronize();
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (auto e : b->ev)
+        if (e) cudaEventDestroy(e);
+    for (int k = 0; k < 2; ++k) {
+        if (b->slot_ev[k]) cudaEventDestroy(b->slot_ev[k]);
+        if (b->h_slot[k]) cudaFreeHost(b->h_slot[k]);
+    }
+    cudaFree(b->d_params);
+    cudaFree(b->d_counters);
+    cudaGetLastError();
+    delete b;
+}
+
+extern "C" gs_status gs_batch_step(gs_batch *b, const gs_attrs *attrs, const gs_grads *grads, const gs_camera *cams,
+                                   const gs_step_params *params, int64_t *n_visible, void *stream)
+{
+    return batch_run(b, attrs, grads, cams, params, n_visible, stream, false);
+}
+
+extern "C" gs_status gs_batch_graph_step(gs_batch *b, const gs_attrs *attrs, const gs_grads *grads,
+                                         const gs_camera *cams, const gs_step_params *params, int64_t *n_visible,
+                                         void *stream)
+{
+    return batch_run(b, attrs, grads, cams, params, n_visible, stream, true);
+}
+
+extern "C" gs_status gs_batch_config(const gs_batch *b, int32_t *tile_rows, int32_t *sh_width,
+                                     int32_t *blocks_per_sm, int32_t *tuned)
+{
+    if (!b) return GS_ERR_INVALID_ARG;
+    int tile = 0, width = 0, mb = 0;
+    gs::batch_candidate_info(b->prec, b->best >= 0 ? b->best : 0, &tile, &width, &mb);
+    if (tile_rows) *tile_rows = tile;
+    if (sh_width) *sh_width = width;
+    if (blocks_per_sm) *blocks_per_sm = mb;
+    if (tuned) *tuned = b->best >= 0 ? 1 : 0;
+    return GS_OK;
+}
 
 // ---------------------------------------------------------------------------
 // gs_step_host_noalloc: the host-gradient step with its staging in a fixed

@@ -143,10 +143,28 @@ __device__ __forceinline__ float step_element(float th, float g, float &m, float
     return fmaf(-lr, u, th);
 }
 
+// Scene table of one batched launch (in device memory, written by one
+// host-to-device copy before each launch or graph replay).
+constexpr int kMaxBatch = 64;
+struct BatchParams {
+    int32_t n_scenes;
+    int32_t total_tiles;
+    int32_t tile_start[kMaxBatch + 1];
+    StepArgs args[kMaxBatch];
+};
+
 // --------------------------------------------------- launch entry points
 // (defined in the kernel translation units, called by api.cu)
 
 cudaError_t launch_step(const StepArgs &a, int prec, int vis_src, cudaStream_t s);
+// Batched launch with candidate configuration `cand` (0 .. batch_candidates-1)
+// over the device scene table p (tile_start built for that candidate's tile
+// size, see batch_candidate_info); *grid receives the persistent grid.  With
+// fn != NULL nothing is launched: *fn receives the kernel (for graph nodes).
+int batch_candidates(int prec);
+void batch_candidate_info(int prec, int cand, int *tile, int *width, int *min_blocks);
+cudaError_t launch_batch(const BatchParams *p, unsigned *work, unsigned *done, int prec, int cand, cudaStream_t s,
+                         int *grid, void **fn);
 cudaError_t launch_visibility(const float *xyz, int32_t n, const float cam[16], uint8_t *mask,
                               int32_t *list, unsigned long long *count, cudaStream_t s);
 cudaError_t launch_bias_table(double beta1, double beta2, int32_t len, double *t1, double *t2,

@@ -19,6 +19,8 @@
 // one item, once.  The storage format of the moments is a template parameter
 // (State<kPrec>): all arithmetic is FP32.
 
+#include <algorithm>
+
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -506,22 +508,21 @@ __device__ __forceinline__ void tile_decide(const StepArgs &a, const int vis_src
 
 // ---------------------------------------------------------------- the kernel
 
-template <int kTile, int kMinBlocks, int kPrec, int kW>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) step_tile(const StepArgs a, const int vis_src)
+// One tile: phase A, then the items of its visible and invisible-sampled rows.
+template <int kTile, int kPrec, int kW>
+__device__ __forceinline__ void process_tile(const StepArgs &a, const int vis_src, const int64_t r0,
+                                             TileLists<kTile> &L)
 {
     static_assert(kTile % kThreads == 0, "tile must be a multiple of the block");
     static_assert(kW == 4 || kW == 8, "SH items cover 4 or 8 columns");
     using S = State<kPrec>;
     constexpr int kNsh = 48 / kW, kItems = kNsh + 3;
-    __shared__ TileLists<kTile> L;
-    const int tid = threadIdx.x;
-    const int64_t r0 = (int64_t)blockIdx.x * kTile;
     int nv, nr;
     tile_decide<kTile, S::kRowBytes, S::kTByte>(a, vis_src, r0, L, nv, nr);
 
     // items grouped by kind: all SH items, then the small items, then RSR
     const int e_sh = kNsh * nv, e_vis = kItems * nv, e_all = e_vis + kItems * nr;
-    for (int w = tid; w < e_all; w += kThreads) {
+    for (int w = threadIdx.x; w < e_all; w += kThreads) {
         if (w < e_sh) {
             const int j = w / kNsh, i = w - j * kNsh;
             const int32_t e = L.list[j];
@@ -536,6 +537,57 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) step_tile(const StepArgs
             const int j = q / kItems, i = q - j * kItems;
             rsr_item<kPrec, kW>(a, L.rlist[j], i);
         }
+    }
+}
+
+template <int kTile, int kMinBlocks, int kPrec, int kW>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) step_tile(const StepArgs a, const int vis_src)
+{
+    __shared__ TileLists<kTile> L;
+    process_tile<kTile, kPrec, kW>(a, vis_src, (int64_t)blockIdx.x * kTile, L);
+}
+
+// Many scenes in one persistent launch.  The scene table lives in device
+// memory (p); CTAs take the next tile of the whole batch from the work
+// counter (tile t belongs to the scene s with tile_start[s] <= t <
+// tile_start[s+1]) until all tiles are done, keeping the current scene's
+// arguments in shared memory.  The last CTA to finish returns both counters
+// to zero, so every launch (and every replay of a captured graph) starts
+// from a clean counter.
+template <int kTile, int kMinBlocks, int kPrec, int kW>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) step_batch(const BatchParams *__restrict__ p,
+                                                                    unsigned *__restrict__ work,
+                                                                    unsigned *__restrict__ done)
+{
+    __shared__ TileLists<kTile> L;
+    __shared__ StepArgs sa;
+    __shared__ int s_tile;
+    const int tid = threadIdx.x;
+    const int total = p->total_tiles, n_scenes = p->n_scenes;
+    int cur = -1;
+    for (;;) {
+        if (tid == 0) s_tile = (int)atomicAdd(work, 1u);
+        __syncthreads();
+        const int t = s_tile;
+        if (t >= total) break;
+        int lo = 0, hi = n_scenes - 1;         // last scene whose first tile is <= t
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (p->tile_start[mid] <= t) lo = mid; else hi = mid - 1;
+        }
+        if (lo != cur) {
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(&p->args[lo]);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(&sa);
+            for (int q = tid; q < (int)(sizeof(StepArgs) / 4); q += kThreads) dst[q] = src[q];
+            cur = lo;
+            __syncthreads();
+        }
+        process_tile<kTile, kPrec, kW>(sa, kVisCamera, (int64_t)(t - p->tile_start[lo]) * kTile, L);
+        __syncthreads();                       // the lists are reused by the next tile
+    }
+    if (tid == 0 && atomicAdd(done, 1u) == gridDim.x - 1) {
+        *work = 0u;
+        *done = 0u;
     }
 }
 
@@ -563,6 +615,87 @@ cudaError_t launch_step(const StepArgs &a, int prec, int vis_src, cudaStream_t s
         return cudaErrorNotSupported;
     }
     return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ batched launch
+namespace {
+
+template <int kTile, int kMinBlocks, int kPrec, int kW>
+cudaError_t launch_batch_t(const BatchParams *p, unsigned *work, unsigned *done, cudaStream_t s, int *grid_out,
+                           void **fn_out)
+{
+    auto k = step_batch<kTile, kMinBlocks, kPrec, kW>;
+    static int s_grid[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    int &grid = s_grid[dev & 63];
+    if (!grid) {
+        int per_sm = 0, sms = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, 0)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        grid = std::max(1, per_sm) * sms;      // persistent: every CTA resident
+    }
+    if (grid_out) *grid_out = grid;
+    if (fn_out) {                              // only report the kernel and its grid
+        *fn_out = reinterpret_cast<void *>(k);
+        return cudaSuccess;
+    }
+    k<<<grid, kThreads, 0, s>>>(p, work, done);
+    return cudaGetLastError();
+}
+
+using BatchFn = cudaError_t (*)(const BatchParams *, unsigned *, unsigned *, cudaStream_t, int *, void **);
+
+struct BatchCandidate {
+    int tile, width, min_blocks;
+    BatchFn fn;
+};
+
+const BatchCandidate kCandF32[] = {
+    {256, 4, 4, launch_batch_t<256, 4, GS_MOM_FP32, 4>}, {512, 4, 4, launch_batch_t<512, 4, GS_MOM_FP32, 4>},
+    {256, 4, 3, launch_batch_t<256, 3, GS_MOM_FP32, 4>}, {256, 8, 4, launch_batch_t<256, 4, GS_MOM_FP32, 8>},
+};
+const BatchCandidate kCandBf16[] = {
+    {256, 8, 4, launch_batch_t<256, 4, GS_MOM_BF16, 8>}, {512, 8, 4, launch_batch_t<512, 4, GS_MOM_BF16, 8>},
+    {256, 4, 4, launch_batch_t<256, 4, GS_MOM_BF16, 4>},
+};
+const BatchCandidate kCandHyb[] = {
+    {256, 8, 4, launch_batch_t<256, 4, GS_MOM_BF16_HYBRID, 8>},
+    {512, 8, 4, launch_batch_t<512, 4, GS_MOM_BF16_HYBRID, 8>},
+    {256, 4, 4, launch_batch_t<256, 4, GS_MOM_BF16_HYBRID, 4>},
+};
+
+const BatchCandidate *candidates(int prec, int *n)
+{
+    switch (prec) {
+    case GS_MOM_FP32: *n = 4; return kCandF32;
+    case GS_MOM_BF16: *n = 3; return kCandBf16;
+    case GS_MOM_BF16_HYBRID: *n = 3; return kCandHyb;
+    default: *n = 0; return nullptr;
+    }
+}
+
+}  // namespace
+
+int batch_candidates(int prec) { int n = 0; candidates(prec, &n); return n; }
+
+void batch_candidate_info(int prec, int c, int *tile, int *width, int *min_blocks)
+{
+    int n = 0;
+    const BatchCandidate *cs = candidates(prec, &n);
+    *tile = cs[c].tile;
+    *width = cs[c].width;
+    *min_blocks = cs[c].min_blocks;
+}
+
+cudaError_t launch_batch(const BatchParams *p, unsigned *work, unsigned *done, int prec, int cand, cudaStream_t s,
+                         int *grid, void **fn)
+{
+    int n = 0;
+    const BatchCandidate *cs = candidates(prec, &n);
+    if (cand < 0 || cand >= n) return cudaErrorInvalidValue;
+    return cs[cand].fn(p, work, done, s, grid, fn);
 }
 
 }  // namespace gs

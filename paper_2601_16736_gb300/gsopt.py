@@ -20,6 +20,7 @@ GS_MOM_FP32, GS_MOM_BF16, GS_MOM_FP8E4M3, GS_MOM_BF16_HYBRID = range(4)
 GS_REG_DAR, GS_REG_COUPLED, GS_REG_ADAMW, GS_REG_ADAMW_CLIP = range(4)
 GROUPS = (("xyz", 3), ("scale", 3), ("rot", 4), ("opacity", 1), ("sh", 48))
 GS_NOALLOC_MAX_ROWS = 65536
+GS_MAX_BATCH = 64
 
 
 class GsError(RuntimeError):
@@ -86,6 +87,12 @@ def _load():
         "gs_bias_table_len": ([P], i64),
         "gs_bias_table": ([P, P, P, i64, P], ctypes.c_int),
         "gs_opt_sync_errors": ([P, P], ctypes.c_int),
+        "gs_batch_create": ([ctypes.POINTER(P), P, i32], ctypes.c_int),
+        "gs_batch_destroy": ([P], None),
+        "gs_batch_step": ([P, P, P, P, P, P, P], ctypes.c_int),
+        "gs_batch_graph_step": ([P, P, P, P, P, P, P], ctypes.c_int),
+        "gs_batch_config": ([P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)],
+                            ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -233,3 +240,62 @@ def gs_bias_table(h, b1, b2, length: int, stream=None) -> None:
 
 def gs_opt_sync_errors(h, stream=None) -> int:
     return _load().gs_opt_sync_errors(h, _stream(stream))
+
+
+# ------------------------------------------------------------------ batches
+
+class Batch:
+    """Host arrays for gs_batch_* (attrs, grads, cameras, params of every
+    scene), built once from per-scene structs and reused across calls."""
+
+    def __init__(self, handles):
+        n = len(handles)
+        self.n = n
+        arr = (ctypes.c_void_p * n)(*[h.value for h in handles])
+        self.h = ctypes.c_void_p()
+        _check(_load().gs_batch_create(ctypes.byref(self.h), arr, n), "gs_batch_create")
+        self.attrs = (gs_attrs * n)()
+        self.grads = (gs_attrs * n)()
+        self.cams = (gs_camera * n)()
+        self.params = (gs_step_params * n)()
+
+    def set(self, s, attrs=None, grads=None, cam=None, params=None):
+        if attrs is not None:
+            self.attrs[s] = attrs
+        if grads is not None:
+            self.grads[s] = grads
+        if cam is not None:
+            self.cams[s] = cam
+        if params is not None:
+            self.params[s] = params
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            _load().gs_batch_destroy(self.h)
+            self.h = None
+
+
+def gs_batch_step(b: Batch, n_visible=None, stream=None, graph: bool = False) -> None:
+    fn = _load().gs_batch_graph_step if graph else _load().gs_batch_step
+    _check(fn(b.h, ctypes.cast(b.attrs, ctypes.c_void_p), ctypes.cast(b.grads, ctypes.c_void_p),
+              ctypes.cast(b.cams, ctypes.c_void_p), ctypes.cast(b.params, ctypes.c_void_p), _ptr(n_visible),
+              _stream(stream)), "gs_batch_graph_step" if graph else "gs_batch_step")
+
+
+def gs_batch_graph_step(b: Batch, n_visible=None, stream=None) -> None:
+    gs_batch_step(b, n_visible, stream, graph=True)
+
+
+def gs_batch_config(b: Batch) -> dict:
+    t, w, m, tuned = (ctypes.c_int32() for _ in range(4))
+    _check(_load().gs_batch_config(b.h, ctypes.byref(t), ctypes.byref(w), ctypes.byref(m), ctypes.byref(tuned)),
+           "gs_batch_config")
+    return dict(tile_rows=t.value, sh_width=w.value, blocks_per_sm=m.value, tuned=bool(tuned.value))
+
+
+def gs_batch_create(handles) -> Batch:
+    return Batch(handles)
+
+
+def gs_batch_destroy(b: Batch) -> None:
+    b.close()

@@ -1,0 +1,108 @@
+"""Batched step (gs_batch_*): one persistent launch over several scenes.
+
+Every scene's result must be bit-identical to gs_step_camera on that scene
+alone — through the autotuning phase (each candidate launch configuration in
+turn) and through the captured graph — and match the FP64 oracle."""
+import numpy as np
+import pytest
+
+from harness import GpuRun, OracleRun, assert_close
+from paper_2601_16736_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+SIZES = [1, 257, 5_003, 40_000, 123_457]
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_2601_16736_gb300 import build
+    build.build()
+    from paper_2601_16736_gb300 import gsopt
+    return gsopt
+
+
+def _scenes(prec_name, G):
+    runs_b, runs_s, cams = [], [], []
+    for i, n in enumerate(SIZES):
+        groups = synth.scene_blobs(n, 1200 + i, [6.0, 12.5, 22.0, 40.0, 75.0][i])
+        rb = GpuRun(groups, prec=getattr(G, "GS_MOM_" + prec_name))
+        rs = GpuRun(groups, prec=getattr(G, "GS_MOM_" + prec_name))
+        g = synth.grads_rows(n, 1300 + i)
+        rb.set_grads(g)
+        rs.set_grads(g)
+        runs_b.append(rb)
+        runs_s.append(rs)
+        cams.append(synth.ring_cameras(10, (0.0, 30.0)))
+    return runs_b, runs_s, cams
+
+
+@pytest.mark.parametrize("prec", ["FP32", "BF16_HYBRID"])
+def test_batch_equals_single_scene_steps(G, prec):
+    runs_b, runs_s, cams = _scenes(prec, G)
+    b = G.gs_batch_create([r.h for r in runs_b])
+    nvis = torch.zeros(len(SIZES), dtype=torch.int64, device="cuda")
+    n_cand = {"FP32": 4, "BF16_HYBRID": 3}[prec]
+    steps = 3 * n_cand + 6                  # tuning, then the tuned eager and graph paths
+    for k in range(1, steps + 1):
+        for s, (rb, rs) in enumerate(zip(runs_b, runs_s)):
+            p = G.make_params(synth.lr_for_step(k, steps), k, restate=(k % 5 == 0), restate_ratio=0.3, seed=s)
+            cam = G.make_camera(cams[s][(k * 7 + s) % len(cams[s])])
+            b.set(s, G.make_attrs(rb.attrs), G.make_attrs(rb.grads), cam, p)
+            rs.step_camera(cams[s][(k * 7 + s) % len(cams[s])], p, mask_out=False)
+            nvis[s] -= rs.nvis[0]
+        G.gs_batch_step(b, nvis, graph=(k > 3 * n_cand + 3))
+    torch.cuda.synchronize()
+    cfg = G.gs_batch_config(b)
+    assert cfg["tuned"]
+    assert int(nvis.abs().sum().item()) == 0          # same visible counts
+    for rb, rs in zip(runs_b, runs_s):
+        assert rb.rows().tobytes() == rs.rows().tobytes()
+        mb, vb, tb = rb.state()
+        ms, vs, ts = rs.state()
+        assert mb.tobytes() == ms.tobytes() and vb.tobytes() == vs.tobytes() and tb.tobytes() == ts.tobytes()
+    b.close()
+    for r in runs_b + runs_s:
+        r.close()
+
+
+def test_batch_matches_oracle(G, orc):
+    sizes = [3_001, 20_011]
+    runs, refs, cams = [], [], []
+    for i, n in enumerate(sizes):
+        groups = synth.scene_blobs(n, 1400 + i, 12.5)
+        runs.append(GpuRun(groups))
+        refs.append(OracleRun(orc, synth.to_rows(groups)))
+        cams.append(synth.ring_cameras(6, (0.0, 30.0)))
+    b = G.gs_batch_create([r.h for r in runs])
+    for k in range(1, 21):
+        for s, (r, ref) in enumerate(zip(runs, refs)):
+            g = synth.grads_rows(sizes[s], 1500 + s, k)
+            r.set_grads(g)
+            lr = synth.lr_for_step(k, 20)
+            cam = cams[s][k % len(cams[s])]
+            b.set(s, G.make_attrs(r.attrs), G.make_attrs(r.grads), G.make_camera(cam),
+                  G.make_params(lr, k, restate=(k == 10), restate_ratio=0.5, seed=7))
+            ref.step(g, ref.visible(cam), lr, True, True, k, restate=(k == 10), ratio=0.5, seed=7)
+        G.gs_batch_step(b)
+        torch.cuda.synchronize()
+    for r, ref in zip(runs, refs):
+        assert_close(r.rows(), ref.st.theta, 1e-4, what="batched scene")
+    b.close()
+    for r in runs:
+        r.close()
+
+
+def test_batch_rejects_bad_sets(G):
+    a = GpuRun(synth.scene_uniform(100, 1600))
+    c = GpuRun(synth.scene_uniform(100, 1601), prec=G.GS_MOM_BF16)
+    with pytest.raises(G.GsError):                 # mixed moment precisions
+        G.gs_batch_create([a.h, c.h])
+    with pytest.raises(G.GsError):                 # more than GS_MAX_BATCH scenes
+        G.gs_batch_create([a.h] * (G.GS_MAX_BATCH + 1))
+    a.close()
+    c.close()
