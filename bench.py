@@ -121,6 +121,23 @@ def _dist():
     return ws, rank, local
 
 
+def replica_seed(base: int, rank: int) -> int:
+    """Each rank steps its own independent scene (weak scaling)."""
+    return base + 1000 * rank
+
+
+def reduce_over_ranks(dist, elapsed: float, units: int, device: str):
+    """Whole-job figures: the slowest rank's time and the units of all ranks."""
+    if dist is None:
+        return elapsed, float(units)
+    import torch
+    t = torch.tensor([elapsed], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(u[0])
+
+
 class Scene:
     """One workload resident on the GPU: attributes, a pool of gradient
     buffers, cameras and the per-step parameters."""
@@ -260,18 +277,11 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     wl = synth.WORKLOADS[args.workload]
-    seed = wl.seed + 1000 * rank
+    seed = replica_seed(wl.seed, rank)
     sc = Scene(G, synth, wl, seed, args.warmup + args.steps)
     r = timed_run(G, sc, args.prec, args.steps, args.warmup, clocks_device=local, dist=dist)
     elapsed, timed_nv = r["elapsed"], r["nv"]
-    if dist is not None:
-        t = torch.tensor([elapsed, float(timed_nv)], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
-        elapsed_all, nv_all = float(tmax[0]), float(t[1])
-    else:
-        elapsed_all, nv_all = elapsed, float(timed_nv)
+    elapsed_all, nv_all = reduce_over_ranks(dist, elapsed, timed_nv, "cuda")
 
     peak, peak_kind = _peaks()
     traffic, traffic_ratio = None, None
