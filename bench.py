@@ -343,6 +343,8 @@ def run_ours(args):
         out["mixed_precision"] = {"workload": f"{mwl.name}: {mwl.n} Gaussians, ~20% visible, {args.mixed_steps} "
                                               f"timed steps per format", "gate": "group relative L2 vs the FP32 step <= 1e-3",
                                   **legs}
+    if rank == 0 and args.reindex:
+        out["reindex"] = reindex_leg(G, synth, args.reindex_steps)
     if rank == 0 and args.batched:
         out["batched"] = batched_leg(G, synth, args.batched_steps)
     if rank == 0 and args.cpu_baseline:
@@ -351,6 +353,80 @@ def run_ours(args):
         print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()
+
+
+HYB_STATE = 2 * (14 * 4 + 45 * 2) + 4     # m, v and t of one row in the hybrid format (B)
+
+
+def reindex_leg(G, synth, steps, prec="bf16_hybrid", n_events=3):
+    """The 6 M workload (about 10 % visible) with BF16-hybrid moments and a
+    row-set change every 100 steps: prune 5 %, clone 5 % (fresh state),
+    relocate 2 % (destination state reset).  Each event re-indexes the
+    library's state (gs_reindex_state) and gathers the attributes into the
+    second attribute buffer (gs_gather_attrs); both run inside the timed
+    region.  The events' index arrays are resident on the device."""
+    import torch
+    wl = synth.WORKLOADS["c5_6m"]
+    warm = wl.restate_every                   # the first event (spare state allocation) is a warm-up
+    sc = Scene(G, synth, wl, wl.seed, warm + steps)
+    other = {k: torch.empty_like(v) for k, v in sc.attrs.items()}
+    bufs = [(sc.attrs, sc.A), (other, G.make_attrs(other))]
+    events = []
+    for e in range(n_events):
+        src, reset, attr_src = synth.reindex_event(wl.n, wl.seed, e)
+        assert src.size == wl.n
+        events.append(dict(src=torch.from_numpy(src).cuda(), reset=torch.from_numpy(reset).cuda(),
+                           attr_src=torch.from_numpy(attr_src).cuda(),
+                           n_copy=int(((src >= 0) & (reset == 0)).sum())))
+    h = G.gs_opt_init(G.make_config(n_pixels=wl.n_pixels, prec=PREC_ENUM[prec]), wl.n)
+    counts = torch.zeros(warm + steps, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+    cur = [0]
+    ev_pairs = []
+    moved = [0.0]
+
+    def step(i, timed):
+        k = i + 1
+        A = bufs[cur[0]][1]
+        G.gs_step_camera(h, A, sc.GB[i % len(sc.GB)], sc.CAMS[sc.order[i]], sc.P[i], n_visible=counts[i:i + 1],
+                         stream=stream)
+        if k % wl.restate_every == 0:
+            ev = events[(k // wl.restate_every) % n_events]
+            if timed:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            G.gs_reindex_state(h, ev["src"], ev["reset"], wl.n, stream=stream)
+            G.gs_gather_attrs(h, A, wl.n, bufs[1 - cur[0]][1], ev["attr_src"], wl.n, stream=stream)
+            cur[0] = 1 - cur[0]
+            if timed:
+                e1.record(stream)
+                ev_pairs.append((e0, e1))
+                moved[0] += ev["n_copy"] * HYB_STATE + wl.n * (HYB_STATE + 5) + wl.n * (2 * 236 + 4)
+
+    for i in range(warm):
+        step(i, False)
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for i in range(warm, warm + steps):
+        step(i, True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    assert G.gs_opt_sync_errors(h) == 0
+    G.gs_opt_destroy(h)
+    elapsed = t0.elapsed_time(t1) / 1e3
+    nv = int(counts[warm:].sum().item())
+    re_s = sum(a.elapsed_time(b) for a, b in ev_pairs) / 1e3
+    res = {"workload": f"{wl.name}: {wl.n} Gaussians, ~{nv / steps / wl.n:.0%} visible, {prec} moments, "
+                       f"re-index every {wl.restate_every} steps (prune 5 %, clone 5 %, relocate 2 %)",
+           "value": nv / elapsed, "unit": UNIT, "steps": steps, "ms_per_step": elapsed / steps * 1e3,
+           "events": len(ev_pairs), "reindex_ms_per_event": re_s / max(len(ev_pairs), 1) * 1e3,
+           "reindex_share_of_time": re_s / elapsed,
+           "reindex_gbs": moved[0] / re_s / 1e9 if re_s > 0 else None,
+           "reindex_bytes_per_event": moved[0] / max(len(ev_pairs), 1)}
+    del sc
+    torch.cuda.empty_cache()
+    return res
 
 
 def batched_leg(G, synth, steps, n_scenes=16, seed=1004):
@@ -511,6 +587,8 @@ def main():
     ap.add_argument("--mixed-steps", type=int, default=300)
     ap.add_argument("--no-mixed-error", dest="mixed_error", action="store_false")
     ap.add_argument("--no-batched", dest="batched", action="store_false")
+    ap.add_argument("--no-reindex", dest="reindex", action="store_false")
+    ap.add_argument("--reindex-steps", type=int, default=1000)
     ap.add_argument("--batched-steps", type=int, default=100)
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the step kernel for this workload (from profiles/)")
