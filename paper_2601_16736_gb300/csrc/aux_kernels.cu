@@ -99,12 +99,12 @@ __global__ void reindex_kernel(const StateView in, int32_t n_in, const StateView
     }
     const bool fresh = s < 0 || (reset && reset[j]);
     uint4 mv = make_uint4(0u, 0u, 0u, 0u), vv = mv;
-    if (!fresh) {
-        mv = *reinterpret_cast<const uint4 *>(static_cast<const char *>(in.m) + (size_t)s * kRowBytes + 16 * c);
-        vv = *reinterpret_cast<const uint4 *>(static_cast<const char *>(in.v) + (size_t)s * kRowBytes + 16 * c);
+    if (!fresh) {      // each row is read once and written once: stream past L2
+        mv = __ldcs(reinterpret_cast<const uint4 *>(static_cast<const char *>(in.m) + (size_t)s * kRowBytes + 16 * c));
+        vv = __ldcs(reinterpret_cast<const uint4 *>(static_cast<const char *>(in.v) + (size_t)s * kRowBytes + 16 * c));
     }
-    *reinterpret_cast<uint4 *>(static_cast<char *>(out.m) + (size_t)j * kRowBytes + 16 * c) = mv;
-    *reinterpret_cast<uint4 *>(static_cast<char *>(out.v) + (size_t)j * kRowBytes + 16 * c) = vv;
+    __stcs(reinterpret_cast<uint4 *>(static_cast<char *>(out.m) + (size_t)j * kRowBytes + 16 * c), mv);
+    __stcs(reinterpret_cast<uint4 *>(static_cast<char *>(out.v) + (size_t)j * kRowBytes + 16 * c), vv);
 }
 
 // ------------------------------------------------------------ export/import
@@ -181,28 +181,40 @@ __global__ void import_kernel(const StateView st, int32_t n, const float *__rest
 
 // ----------------------------------------------------------- attribute gather
 // One thread per (output row, canonical column).
+// 16 lanes per output row: lanes 0-11 move the 12 float4 of the SH row,
+// lane 12 the rotation float4, lanes 13-15 xyz, scale and opacity.  Nothing
+// is read again, so loads and stores stream past L2.
+constexpr int kGatherLanes = 16;
+
 __global__ void gather_attrs_kernel(const gs_attrs in, int32_t n_in, const gs_attrs out,
                                     const int32_t *__restrict__ src, int32_t n_new, int32_t *err)
 {
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= (int64_t)n_new * kNumCols) return;
-    const int64_t j = gid / kNumCols;
-    const int c = (int)(gid - j * kNumCols);
+    const int64_t j = gid / kGatherLanes;
+    const int c = (int)(gid % kGatherLanes);
+    if (j >= n_new) return;
     const int32_t s = src[j];
     if (s < 0) return;
     if (s >= n_in) {
         if (c == 0) record_error(err, GS_ERR_INVALID_ARG);
         return;
     }
-    const float *ip;
-    float *op;
-    int w, k;
-    if (c < 3) { ip = in.xyz; op = out.xyz; w = 3; k = c; }
-    else if (c < 6) { ip = in.scale; op = out.scale; w = 3; k = c - 3; }
-    else if (c < 10) { ip = in.rot; op = out.rot; w = 4; k = c - 6; }
-    else if (c == 10) { ip = in.opacity; op = out.opacity; w = 1; k = 0; }
-    else { ip = in.sh; op = out.sh; w = 48; k = c - 11; }
-    op[j * w + k] = ip[(int64_t)s * w + k];
+    if (c < 12) {
+        const float4 x = __ldcs(reinterpret_cast<const float4 *>(in.sh) + (int64_t)s * 12 + c);
+        __stcs(reinterpret_cast<float4 *>(out.sh) + j * 12 + c, x);
+    } else if (c == 12) {
+        __stcs(reinterpret_cast<float4 *>(out.rot) + j, __ldcs(reinterpret_cast<const float4 *>(in.rot) + s));
+    } else if (c == 15) {
+        __stcs(out.opacity + j, __ldcs(in.opacity + s));
+    } else {
+        const float *ip = c == 13 ? in.xyz : in.scale;
+        float *op = c == 13 ? out.xyz : out.scale;
+        const float a = __ldcs(ip + (int64_t)s * 3), b = __ldcs(ip + (int64_t)s * 3 + 1),
+                    d = __ldcs(ip + (int64_t)s * 3 + 2);
+        __stcs(op + j * 3, a);
+        __stcs(op + j * 3 + 1, b);
+        __stcs(op + j * 3 + 2, d);
+    }
 }
 
 unsigned blocks_for(int64_t n_threads) { return (unsigned)((n_threads + kThreads - 1) / kThreads); }
@@ -269,7 +281,7 @@ cudaError_t launch_gather_attrs(const gs_attrs &in, int32_t n_in, const gs_attrs
                                 int32_t n_new, int32_t *err, cudaStream_t s)
 {
     if (n_new <= 0) return cudaSuccess;
-    gather_attrs_kernel<<<blocks_for((int64_t)n_new * kNumCols), kThreads, 0, s>>>(in, n_in, out, src, n_new, err);
+    gather_attrs_kernel<<<blocks_for((int64_t)n_new * kGatherLanes), kThreads, 0, s>>>(in, n_in, out, src, n_new, err);
     return cudaGetLastError();
 }
 

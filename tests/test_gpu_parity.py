@@ -284,17 +284,37 @@ def test_reindex_out_of_range_is_reported_not_read(G):
     run.close()
 
 
-def test_gather_attrs(G):
-    n = 7001
-    groups = synth.scene_uniform(n, 730)
+@pytest.mark.parametrize("n", [1, 17, 7001])
+def test_gather_attrs(G, n):
+    groups = synth.scene_uniform(n, 730 + n)
     run = GpuRun(groups)
     src, reset, attr_src = synth.reindex_event(n, 731, 0)
-    out = {k: torch.zeros((attr_src.size, v.shape[1]), dtype=torch.float32, device="cuda") for k, v in groups.items()}
+    attr_src = attr_src.copy()
+    if attr_src.size > 2:
+        attr_src[1] = -1                     # a negative entry leaves the output row untouched
+    sentinel = -7.5
+    out = {k: torch.full((attr_src.size, v.shape[1]), sentinel, dtype=torch.float32, device="cuda")
+           for k, v in groups.items()}
     G.gs_gather_attrs(run.h, G.make_attrs(run.attrs), n, G.make_attrs(out), torch.from_numpy(attr_src).cuda(),
                       attr_src.size)
     torch.cuda.synchronize()
+    assert G.gs_opt_sync_errors(run.h) == G.GS_OK
     for k, v in groups.items():
-        assert np.array_equal(out[k].cpu().numpy(), v[attr_src])
+        got = out[k].cpu().numpy()
+        ok = attr_src >= 0
+        assert np.array_equal(got[ok], v[attr_src[ok]])
+        assert np.all(got[~ok] == sentinel)
+    # an out-of-range source is skipped and reported by the next sync
+    bad = np.zeros(5, np.int32)
+    bad[3] = n + 4
+    out2 = {k: torch.full((5, v.shape[1]), sentinel, dtype=torch.float32, device="cuda") for k, v in groups.items()}
+    G.gs_gather_attrs(run.h, G.make_attrs(run.attrs), n, G.make_attrs(out2), torch.from_numpy(bad).cuda(), 5)
+    torch.cuda.synchronize()
+    assert G.gs_opt_sync_errors(run.h) == G.GS_ERR_INVALID_ARG
+    for k, v in groups.items():
+        got = out2[k].cpu().numpy()
+        assert np.all(got[3] == sentinel)
+        assert np.array_equal(got[[0, 1, 2, 4]], v[[0, 0, 0, 0]])
     run.close()
 
 
