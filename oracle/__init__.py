@@ -54,6 +54,32 @@ class _Config(ctypes.Structure):
     ]
 
 
+class _Ext(ctypes.Structure):
+    _fields_ = [
+        ("noise_mode", ctypes.c_int32), ("aiu", ctypes.c_int32),
+        ("noise_lr", ctypes.c_double), ("noise_k", ctypes.c_double), ("noise_t", ctypes.c_double),
+        ("aiu_prob", ctypes.c_double), ("aiu_scale", ctypes.c_double), ("seed", ctypes.c_uint64),
+    ]
+
+
+@dataclass
+class Ext:
+    """Position noise (App. Eq. disentangled_mu) and AIU (Sec. 3.2) switches
+    of one iteration.  noise_mode: 0 off, 1 visible primitives, 2 all."""
+    noise_mode: int = 0
+    aiu: bool = False
+    noise_lr: float = 5e5
+    noise_k: float = 100.0
+    noise_t: float = 0.005
+    aiu_prob: float = 0.0
+    aiu_scale: float = 1.0
+    seed: int = 0
+
+    def _c(self) -> _Ext:
+        return _Ext(int(self.noise_mode), int(bool(self.aiu)), self.noise_lr, self.noise_k, self.noise_t,
+                    self.aiu_prob, self.aiu_scale, self.seed & (2**64 - 1))
+
+
 @dataclass
 class Config:
     """Static hyper-parameters; defaults are the paper's (App. "Hyperparameter
@@ -102,6 +128,21 @@ def lib():
         L.orc_reindex.restype = i32
         L.orc_bias_denominators.argtypes = [f64, i64, P]
         L.orc_bias_denominators.restype = None
+        L.orc_aiu_sampled.argtypes = [u64, i64, i64, f64]
+        L.orc_aiu_sampled.restype = i32
+        L.orc_gauss3.argtypes = [u64, i64, i64, P]
+        L.orc_gauss3.restype = None
+        L.orc_covariance.argtypes = [P, P, P]
+        L.orc_covariance.restype = None
+        L.orc_noise_term.argtypes = [P, f64, f64, f64, f64, P, P]
+        L.orc_noise_term.restype = None
+        L.orc_is_active.argtypes = [f64]
+        L.orc_is_active.restype = i32
+        L.orc_active_rows.argtypes = [P, i64, P]
+        L.orc_active_rows.restype = i64
+        L.orc_step_ext.argtypes = [ctypes.POINTER(_Config), i64, P, P, P, P, P, P, P, i32, i32, i64, i64,
+                                   ctypes.POINTER(_Ext), P]
+        L.orc_step_ext.restype = i64
         _lib = L
     return _lib
 
@@ -206,3 +247,61 @@ def bias_denominators(beta: float, length: int) -> np.ndarray:
     out = np.zeros(length, np.float64)
     lib().orc_bias_denominators(float(beta), int(length), _ptr(out))
     return out
+
+
+# ------------------------------------------- position noise, AIU, N_a / N_d
+
+def aiu_sampled(seed: int, k: int, rows, prob: float) -> np.ndarray:
+    """AIU membership of each row (stream tag 1)."""
+    L = lib()
+    return np.array([L.orc_aiu_sampled(seed & (2**64 - 1), int(k), int(r), float(prob)) for r in rows], np.uint8)
+
+
+def gauss3(seed: int, k: int, row: int) -> np.ndarray:
+    """The noise draw gamma ~ N(0, I_3) of one row and iteration."""
+    g = np.zeros(3, np.float64)
+    lib().orc_gauss3(seed & (2**64 - 1), int(k), int(row), _ptr(g))
+    return g
+
+
+def covariance(q, kappa) -> np.ndarray:
+    q = _req(q, np.float64, (4,))
+    kappa = _req(kappa, np.float64, (3,))
+    out = np.zeros(9, np.float64)
+    lib().orc_covariance(_ptr(q), _ptr(kappa), _ptr(out))
+    return out.reshape(3, 3)
+
+
+def noise_term(row, eta_ro: float, eta_mu: float, lam_mu: float, lam_t: float, gamma) -> np.ndarray:
+    row = _req(row, np.float64, (NCOL,))
+    gamma = _req(gamma, np.float64, (3,))
+    out = np.zeros(3, np.float64)
+    lib().orc_noise_term(_ptr(row), float(eta_ro), float(eta_mu), float(lam_mu), float(lam_t), _ptr(gamma),
+                         _ptr(out))
+    return out
+
+
+def is_active(tau: float) -> bool:
+    return bool(lib().orc_is_active(float(tau)))
+
+
+def active_rows(tau) -> np.ndarray:
+    """Ascending indices of the active rows (opacity > 1/255) of FP32 logits."""
+    tau = _req(tau, np.float32)
+    out = np.zeros(max(tau.size, 1), np.int32)
+    c = lib().orc_active_rows(_ptr(tau), tau.size, _ptr(out))
+    return out[:c].copy()
+
+
+def step_ext(cfg: Config, st: State, grad, mask, lr, dar_o: bool, dar_s: bool, k: int, ext: Ext,
+             row_ids=None, n_visible: int = 0) -> int:
+    """orc_step with the position noise and AIU; returns N_a after the step."""
+    grad = _req(grad, np.float32, (st.n, NCOL))
+    mask_a = None if mask is None else _req(mask, np.uint8, (st.n,))
+    lr = _req(lr, np.float64, (6,))
+    ids = None if row_ids is None else _req(row_ids, np.int64, (st.n,))
+    c = cfg._c()
+    x = ext._c()
+    return lib().orc_step_ext(ctypes.byref(c), st.n, _ptr(st.theta), _ptr(grad), _ptr(st.m), _ptr(st.v),
+                              _ptr(st.t), _ptr(mask_a), _ptr(lr), int(bool(dar_o)), int(bool(dar_s)), int(k),
+                              int(n_visible), ctypes.byref(x), _ptr(ids))

@@ -308,3 +308,175 @@ void orc_bias_denominators(double beta, int64_t len, double *out)
 {
     for (int64_t k = 0; k < len; ++k) out[k] = 1.0 - pow(beta, (double)k);
 }
+
+/* ------------------------------------------- position noise, AIU, N_a / N_d */
+
+/*
+ * Random streams.  All draws come from the SplitMix64 stream of the step's
+ * seed; the top two bits of the counter name the use, so no two uses share a
+ * draw: 0 = StSS membership (orc_stss_sampled, iteration k < 2^30), 1 = AIU
+ * membership, 2 and 3 = the two words behind the position noise.  Bits 32-61
+ * carry the iteration k, bits 0-31 the row.
+ */
+static uint64_t orc_counter(uint64_t tag, int64_t k, int64_t row)
+{
+    return (tag << 62) | ((uint64_t)k << 32) | (uint64_t)(uint32_t)row;
+}
+
+/*
+ * AIU membership (Sec. 3.2, "Artificial Implicit Update"): a uniform sampler
+ * over the invisible primitives, read as an independent Bernoulli(prob) draw
+ * per primitive and iteration on stream tag 1 (top 53 bits as a fraction of
+ * 2^53, sampled iff below prob).
+ */
+int32_t orc_aiu_sampled(uint64_t seed, int64_t k, int64_t row, double prob)
+{
+    uint64_t h = orc_splitmix64_at(seed, orc_counter(1, k, row));
+    double u = (double)(h >> 11) * (1.0 / 9007199254740992.0);
+    return u < prob;
+}
+
+/*
+ * gamma ~ N(0, I_3) of App. Eq. disentangled_mu, by the Box-Muller transform
+ * (Box & Muller, Ann. Math. Stat. 1958).  Each of two SplitMix64 words
+ * (tags 2 and 3) gives two 24-bit uniforms: ua = (bits 40..63 + 1) / 2^24 in
+ * (0, 1] and ub = (bits 16..39) / 2^24 in [0, 1).  Then
+ *   gamma0 = sqrt(-2 ln ua1) cos(2 pi ub1),  gamma1 = sqrt(-2 ln ua1) sin(2 pi ub1),
+ *   gamma2 = sqrt(-2 ln ua2) cos(2 pi ub2).
+ * The uniforms are exact in FP32 and FP64 alike; the transform runs in FP64.
+ */
+void orc_gauss3(uint64_t seed, int64_t k, int64_t row, double g[3])
+{
+    const double inv24 = 1.0 / 16777216.0;
+    const double pi = 3.14159265358979323846;
+    uint64_t h1 = orc_splitmix64_at(seed, orc_counter(2, k, row));
+    uint64_t h2 = orc_splitmix64_at(seed, orc_counter(3, k, row));
+    double ua1 = (double)((h1 >> 40) + 1u) * inv24, ub1 = (double)((h1 >> 16) & 0xFFFFFFu) * inv24;
+    double ua2 = (double)((h2 >> 40) + 1u) * inv24, ub2 = (double)((h2 >> 16) & 0xFFFFFFu) * inv24;
+    double r1 = sqrt(-2.0 * log(ua1)), r2 = sqrt(-2.0 * log(ua2));
+    g[0] = r1 * cos(2.0 * pi * ub1);
+    g[1] = r1 * sin(2.0 * pi * ub1);
+    g[2] = r2 * cos(2.0 * pi * ub2);
+}
+
+/*
+ * Covariance of a primitive, Sigma = R S S^T R^T, S = diag(exp(kappa)), R the
+ * rotation of the quaternion q = (w, x, y, z) (real part first) after
+ * normalisation q / max(|q|, 1e-12).  Row-major 3x3.
+ */
+void orc_covariance(const double q[4], const double kappa[3], double sig[9])
+{
+    double nrm = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    if (nrm < 1e-12) nrm = 1e-12;
+    const double w = q[0] / nrm, x = q[1] / nrm, y = q[2] / nrm, z = q[3] / nrm;
+    const double R[9] = {1.0 - 2.0 * (y * y + z * z), 2.0 * (x * y - w * z),       2.0 * (x * z + w * y),
+                         2.0 * (x * y + w * z),       1.0 - 2.0 * (x * x + z * z), 2.0 * (y * z - w * x),
+                         2.0 * (x * z - w * y),       2.0 * (y * z + w * x),       1.0 - 2.0 * (x * x + y * y)};
+    double s2[3];
+    for (int j = 0; j < 3; ++j) s2[j] = exp(2.0 * kappa[j]);
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double acc = 0.0;
+            for (int j = 0; j < 3; ++j) acc += R[3 * a + j] * s2[j] * R[3 * b + j];
+            sig[3 * a + b] = acc;
+        }
+}
+
+/*
+ * Position noise of App. Eq. disentangled_mu for one primitive (its 59
+ * values before this iteration's update), the amount subtracted from mu:
+ *   R_mu = eta_mu * sigmoid(-lambda_mu (o - lambda_t)) * Sigma gamma,  o = sigmoid(tau);
+ * the bracket of Eq. disentangled_mu scales R_mu by eta_Ro / eta_mu and the
+ * outer factor by eta_mu, which leaves eta_Ro * R_mu.
+ */
+void orc_noise_term(const double *row, double eta_ro, double eta_mu, double lam_mu, double lam_t,
+                    const double gamma[3], double out[3])
+{
+    double sig[9];
+    orc_covariance(row + 6, row + 3, sig);
+    const double o = 1.0 / (1.0 + exp(-row[10]));
+    const double gate = 1.0 / (1.0 + exp(lam_mu * (o - lam_t)));
+    for (int a = 0; a < 3; ++a) {
+        double acc = 0.0;
+        for (int j = 0; j < 3; ++j) acc += sig[3 * a + j] * gamma[j];
+        out[a] = eta_ro * eta_mu * gate * acc;
+    }
+}
+
+/* Active primitive (Sec. 4, "Dataset and Metric"): opacity sigmoid(tau) >
+ * 1/255; dead otherwise. */
+int32_t orc_is_active(double tau)
+{
+    return 1.0 / (1.0 + exp(-tau)) > 1.0 / 255.0;
+}
+
+/* The active rows among n opacity logits (FP32, as stored), ascending, into
+ * rows (may be NULL); returns their number N_a (N_d = n - N_a). */
+int64_t orc_active_rows(const float *tau, int64_t n, int32_t *rows)
+{
+    int64_t c = 0;
+    for (int64_t i = 0; i < n; ++i)
+        if (orc_is_active((double)tau[i])) {
+            if (rows) rows[c] = (int32_t)i;
+            ++c;
+        }
+    return c;
+}
+
+/* Switches and constants of the noise and AIU terms for one iteration. */
+typedef struct {
+    int32_t noise_mode;    /* 0 off, 1 visible primitives, 2 every primitive       */
+    int32_t aiu;           /* AIU active this iteration                            */
+    double noise_lr;       /* eta_Ro                                               */
+    double noise_k;        /* lambda_mu                                            */
+    double noise_t;        /* lambda_t                                             */
+    double aiu_prob;       /* Pro_AIU                                              */
+    double aiu_scale;      /* eta_AIU                                              */
+    uint64_t seed;         /* stream seed (row ids as in orc_restate)              */
+} orc_ext;
+
+/*
+ * orc_step extended by the position noise, AIU and the active count; returns
+ * N_a after the iteration.  Per primitive (global id from row_ids, NULL =
+ * local index):
+ *   visible: the orc_step update, and with noise_mode >= 1 mu -= the noise
+ *     term of the primitive's values before this update (eta_mu = lr[0]);
+ *   invisible, AIU on and sampled, with a step count t > 0 (a primitive never
+ *     seen has no moments): theta -= lr_group * eta_AIU * m^ / (sqrt(v^) + eps)
+ *     from its current moments and t (global k when bias_mode = 1); m, v and t
+ *     are kept (Sec. 3.2: moments unchanged while invisible); no DAR;
+ *   invisible with noise_mode = 2: mu -= the noise term as above.
+ */
+int64_t orc_step_ext(const orc_config *cfg, int64_t n, double *theta, const float *grad,
+                     double *m, double *v, uint32_t *t, const uint8_t *mask,
+                     const double *lr, int32_t dar_o, int32_t dar_s, int64_t k, int64_t n_visible,
+                     const orc_ext *x, const int64_t *row_ids)
+{
+    int64_t active = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t gid = row_ids ? row_ids[i] : i;
+        double *th = theta + i * ORC_NCOL;
+        double *mi = m + i * ORC_NCOL, *vi = v + i * ORC_NCOL;
+        double old[ORC_NCOL];
+        memcpy(old, th, sizeof(old));
+        const int vis = !mask || mask[i];
+        if (vis) {
+            orc_step(cfg, 1, th, grad + i * ORC_NCOL, mi, vi, t + i, NULL, lr, dar_o, dar_s, k, n_visible);
+        } else if (x->aiu && orc_aiu_sampled(x->seed, k, gid, x->aiu_prob) && (cfg->bias_mode || t[i] > 0)) {
+            const double tt = cfg->bias_mode ? (double)k : (double)t[i];
+            const double bc1 = 1.0 - pow(cfg->beta1, tt), bc2 = 1.0 - pow(cfg->beta2, tt);
+            for (int c = 0; c < ORC_NCOL; ++c) {
+                const double u = (mi[c] / bc1) / (sqrt(vi[c] / bc2) + cfg->eps);
+                th[c] -= lr[lr_group(c)] * x->aiu_scale * u;
+            }
+        }
+        if (x->noise_mode == 2 || (x->noise_mode == 1 && vis)) {
+            double g[3], d[3];
+            orc_gauss3(x->seed, k, gid, g);
+            orc_noise_term(old, x->noise_lr, lr[0], x->noise_k, x->noise_t, g, d);
+            for (int a = 0; a < 3; ++a) th[a] -= d[a];
+        }
+        active += orc_is_active(th[10]);
+    }
+    return active;
+}
