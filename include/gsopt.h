@@ -49,7 +49,7 @@
 extern "C" {
 #endif
 
-#define GS_ABI_VERSION 1
+#define GS_ABI_VERSION 2
 #define GS_NUM_COLS 59
 
 typedef enum gs_status {
@@ -91,6 +91,16 @@ typedef enum gs_reg_mode {
     GS_REG_ADAMW_CLIP = 3
 } gs_reg_mode;
 
+/* Which primitives take the position noise of App. Eq. disentangled_mu.  The
+ * equation writes it as a term of the visible primitives' update
+ * (GS_NOISE_VISIBLE); the 3DGS-MCMC regulariser it is taken from moves every
+ * primitive (GS_NOISE_ALL). */
+typedef enum gs_noise_mode {
+    GS_NOISE_OFF = 0,
+    GS_NOISE_VISIBLE = 1,
+    GS_NOISE_ALL = 2
+} gs_noise_mode;
+
 typedef struct gs_attrs {        /* device, caller-owned, updated in place */
     float *xyz, *scale, *rot, *opacity, *sh;
 } gs_attrs;
@@ -128,7 +138,41 @@ typedef struct gs_camera {
     float tan_half_fovx, tan_half_fovy, znear, zfar;
 } gs_camera;
 
-/* Per-iteration parameters. */
+/* Per-iteration parameters.
+ *
+ * Random draws.  Every draw is output number `counter` of the SplitMix64
+ * stream seeded with `seed` (state seed + (counter + 1) * 0x9E3779B97F4A7C15,
+ * then the published finaliser), with counter = tag << 62 | k << 32 | row:
+ *   tag 0  StSS membership: sampled iff the top 53 bits, read as a fraction
+ *          of 2^53, are below restate_ratio;
+ *   tag 1  AIU membership: the same test against aiu_prob;
+ *   tag 2, 3  the noise vector gamma ~ N(0, I_3) by the Box-Muller transform:
+ *          from each word w, ua = (w >> 40 + 1) / 2^24 and
+ *          ub = ((w >> 16) & 0xFFFFFF) / 2^24; with (ua1, ub1) from tag 2 and
+ *          (ua2, ub2) from tag 3, gamma = (r1 cos 2 pi ub1, r1 sin 2 pi ub1,
+ *          r2 cos 2 pi ub2), r = sqrt(-2 ln ua) (FP32 on the device).
+ *
+ * Position noise (App. Eq. disentangled_mu): the chosen primitives'
+ * positions move by -noise_lr * lr[0] * sigmoid(-noise_k (o - noise_t)) *
+ * Sigma gamma, with o = sigmoid(tau), Sigma = R diag(exp(2 kappa)) R^T and R
+ * the rotation of the normalised quaternion (w, x, y, z) (q / max(|q|,
+ * 1e-12)), all taken from the primitive's values before this step's update.
+ * The paper gives no values for noise_lr, noise_k, noise_t (3DGS-MCMC: 5e5,
+ * 100, 0.005).
+ *
+ * AIU (Sec. 3.2): each invisible primitive is sampled with probability
+ * aiu_prob; a sampled one whose step count t is non-zero (per-primitive
+ * mode; any, with bias_mode 1) moves by -lr_group * aiu_scale *
+ * m^/(sqrt(v^) + eps) from its current moments, bias-corrected with its t
+ * (or k), which all stay unchanged.  No regulariser applies to that step.
+ *
+ * n_active: the number of primitives whose opacity sigmoid(tau) exceeds
+ * 1/255 after the step (Sec. 4: active; the others are dead) is added to
+ * this device int64.  The decision is exact: tau > -ln 254 for FP32 tau.
+ *
+ * The batched entry points (gs_batch_*) reject noise, AIU and n_active with
+ * GS_ERR_UNSUPPORTED.
+ */
 typedef struct gs_step_params {
     float lr[6];             /* xyz, scale, rot, opacity, SH DC (sh cols 0-2), SH rest   */
     int32_t dar_opacity;     /* apply the opacity regulariser this step                   */
@@ -136,12 +180,19 @@ typedef struct gs_step_params {
     int32_t restate;         /* apply RSR to the StSS-sampled rows after this step        */
     int32_t reserved;        /* must be 0                                                  */
     double restate_ratio;    /* StSS sampling probability in [0, 1]                        */
-    uint64_t seed;           /* StSS stream seed                                           */
-    int64_t iteration;       /* global iteration k >= 1: keys the StSS draw (row sampled iff
-                                the top 53 bits of SplitMix64(seed, counter k<<32 | row),
-                                read as a fraction of 2^53, are below restate_ratio), and is
-                                the bias-correction step when bias_mode = 1                */
+    uint64_t seed;           /* seed of every random draw of the step (see above)          */
+    int64_t iteration;       /* global iteration k, 1 <= k < 2^30: keys the random draws and
+                                is the bias-correction step when bias_mode = 1             */
     int64_t n_visible;       /* N_v for GS_REG_COUPLED (host-known visible count), else 0  */
+    int32_t noise;           /* gs_noise_mode                                              */
+    int32_t aiu;             /* apply AIU this step                                        */
+    float noise_lr;          /* eta_Ro of Eq. disentangled_mu, finite                      */
+    float noise_k;           /* lambda_mu, finite                                          */
+    float noise_t;           /* lambda_t, finite                                           */
+    float aiu_prob;          /* Pro_AIU in [0, 1]                                          */
+    float aiu_scale;         /* eta_AIU, finite                                            */
+    int32_t reserved2;       /* must be 0                                                  */
+    int64_t *n_active;       /* device int64, optional (NULL): N_a is added to it          */
 } gs_step_params;
 
 typedef struct gs_opt gs_opt;   /* opaque context */
@@ -348,6 +399,20 @@ gs_status gs_opt_export_state(gs_opt *opt, float *m, float *v, uint32_t *t, void
  * unchanged.  Low-precision moments are re-encoded. */
 gs_status gs_opt_import_state(gs_opt *opt, const float *m, const float *v, const uint32_t *t,
                               void *stream);
+
+/*
+ * The active primitives (opacity sigmoid(tau) > 1/255, Sec. 4 "Dataset and
+ * Metric"; exactly tau > -ln 254 for FP32 tau) of the context's n_rows, in
+ * ascending order: the source list of a prune of the dead primitives, ready
+ * for gs_reindex_state (n_new = the count) and gs_gather_attrs.
+ *   opacity  device [n_rows] float32 logits tau, read-only.
+ *   rows     device [n_rows] int32 out, optional (NULL: count only).
+ *   n_active device int64 out (overwritten), required.
+ * Three launches (per-block counts, a scan over the blocks, the ordered
+ * write); a scratch array of one int32 per 1024 rows is kept by the context
+ * (allocated synchronously on first use or growth).
+ */
+gs_status gs_active_rows(gs_opt *opt, const float *opacity, int32_t *rows, int64_t *n_active, void *stream);
 
 /* Length of the context's bias-correction table: the first step count k at
  * which both FP32 factors 1/(1 - beta1^k) and 1/sqrt(1 - beta2^k) round to

@@ -34,6 +34,8 @@ struct gs_opt {
     int64_t staging_rows = 0;
     unsigned long long *count = nullptr;   // device counter for gs_step_host
     unsigned long long *count_host = nullptr;  // pinned
+    int32_t *act_blk = nullptr;   // gs_active_rows scratch, act_blk_len entries
+    int64_t act_blk_len = 0;
     double n_i = 0.0;
     bool latched = false;
     // cache of validated device allocation ranges [base, end)
@@ -187,15 +189,31 @@ gs_status alloc_state(gs_opt *o, int64_t rows, void **m, void **v)
 
 gs::StateView view(const gs_opt *o) { return gs::StateView{o->cfg.prec, o->m, o->v}; }
 
-bool params_ok(const gs_opt *o, const gs_step_params *p)
+bool params_ok(gs_opt *o, const gs_step_params *p)
 {
-    if (!p || p->reserved != 0) return false;
+    if (!p || p->reserved != 0 || p->reserved2 != 0) return false;
     for (int i = 0; i < 6; ++i)
         if (!finite(p->lr[i])) return false;
     if (p->restate && !(p->restate_ratio >= 0.0 && p->restate_ratio <= 1.0)) return false;
-    if (p->iteration < 1 || p->iteration >= ((int64_t)1 << 32)) return false;
+    // k fills bits 32-61 of the draw counters
+    if (p->iteration < 1 || p->iteration >= ((int64_t)1 << 30)) return false;
+    if (p->noise < GS_NOISE_OFF || p->noise > GS_NOISE_ALL) return false;
+    if (p->noise && !(finite(p->noise_lr) && finite(p->noise_k) && finite(p->noise_t))) return false;
+    if (p->aiu != 0 && p->aiu != 1) return false;
+    if (p->aiu && !(p->aiu_prob >= 0.f && p->aiu_prob <= 1.f && finite(p->aiu_scale))) return false;
+    if (!dev_ok(o, p->n_active, p->n_active ? 8 : 0, 8)) return false;
     if (o->cfg.reg_mode == GS_REG_COUPLED && (p->dar_opacity || p->dar_scale) && p->n_visible <= 0) return false;
     return true;
+}
+
+// sigmoid(tau) > 1/255  <=>  tau > -ln 254.  For FP32 tau the test
+// tau > c with c the largest float below -ln 254 decides it exactly.
+float active_threshold()
+{
+    const double t = -log(254.0);
+    float c = (float)t;
+    if ((double)c >= t) c = nextafterf(c, -INFINITY);
+    return c;
 }
 
 void fill_args(const gs_opt *o, const gs_step_params *p, StepArgs *a)
@@ -233,6 +251,15 @@ void fill_args(const gs_opt *o, const gs_step_params *p, StepArgs *a)
     a->k_ctr = (uint64_t)p->iteration;
     // sampled iff (draw >> 11) * 2^-53 < ratio  <=>  (draw >> 11) < ceil(ratio * 2^53)
     a->rs_thr = p->restate ? (uint64_t)ceil(p->restate_ratio * 9007199254740992.0) : 0ull;
+    a->noise = p->noise;
+    a->noise_scale = (float)((double)p->noise_lr * (double)p->lr[0]);
+    a->noise_k = p->noise_k;
+    a->noise_t = p->noise_t;
+    a->aiu = p->aiu;
+    a->aiu_scale = p->aiu_scale;
+    a->aiu_thr = p->aiu ? (uint64_t)ceil((double)p->aiu_prob * 9007199254740992.0) : 0ull;
+    a->n_active = reinterpret_cast<unsigned long long *>(p->n_active);
+    a->tau_act = active_threshold();
 }
 
 template <class A>
@@ -338,6 +365,7 @@ void gs_opt_destroy(gs_opt *o)
     cudaFree(o->err);
     cudaFree(o->staging);
     cudaFree(o->count);
+    cudaFree(o->act_blk);
     if (o->count_host) cudaFreeHost(o->count_host);
     cudaGetLastError();
     if (prev >= 0) cudaSetDevice(prev);
@@ -504,6 +532,28 @@ gs_status gs_gather_attrs(gs_opt *o, const gs_attrs *in, int64_t n_in, const gs_
                                                 static_cast<cudaStream_t>(stream)));
 }
 
+gs_status gs_active_rows(gs_opt *o, const float *opacity, int32_t *rows, int64_t *n_active, void *stream)
+{
+    gs_status st = precheck(o);
+    if (st != GS_OK) return st;
+    const int64_t n = o->n_rows;
+    if (!n_active || !dev_ok(o, n_active, 8, 8) || !dev_ok(o, opacity, 4 * (size_t)n, 4) ||
+        !dev_ok(o, rows, rows ? 4 * (size_t)n : 0, 4) || (n && !opacity))
+        return GS_ERR_INVALID_ARG;
+    const int64_t need = gs::active_rows_scratch(n);
+    if (need > o->act_blk_len) {
+        cudaError_t e = cudaFree(o->act_blk);
+        o->act_blk = nullptr;
+        o->act_blk_len = 0;
+        if (e == cudaSuccess) e = cudaMalloc(&o->act_blk, (size_t)need * sizeof(int32_t));
+        if (e != cudaSuccess) return fail_cuda(o, e);
+        o->act_blk_len = need;
+    }
+    return fail_cuda(o, gs::launch_active_rows(opacity, (int32_t)n, active_threshold(), o->act_blk, rows,
+                                               reinterpret_cast<long long *>(n_active),
+                                               static_cast<cudaStream_t>(stream)));
+}
+
 gs_status gs_opt_export_state(gs_opt *o, float *m, float *v, uint32_t *t, void *stream)
 {
     gs_status st = precheck(o);
@@ -593,6 +643,7 @@ gs_status batch_check(gs_batch *b, const gs_attrs *attrs, const gs_grads *grads,
         gs_status st = precheck(o);
         if (st != GS_OK) return st;
         if (!camera_ok(&cams[s]) || !params_ok(o, &params[s])) return GS_ERR_INVALID_ARG;
+        if (params[s].noise || params[s].aiu || params[s].n_active) return GS_ERR_UNSUPPORTED;
         if (!attrs_ok(o, attrs[s], o->n_rows) || !attrs_ok(o, grads[s], o->n_rows)) return GS_ERR_INVALID_ARG;
     }
     if (!dev_ok(b->scenes[0], n_visible, n_visible ? 8 * (size_t)n : 0, 8)) return GS_ERR_INVALID_ARG;

@@ -3,6 +3,8 @@
 // re-indexing across row-set changes, canonical-layout export/import, and
 // the attribute gather that accompanies a re-index.
 
+#include <algorithm>
+
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -217,6 +219,89 @@ __global__ void gather_attrs_kernel(const gs_attrs in, int32_t n_in, const gs_at
     }
 }
 
+// ------------------------------------------------------------ active rows
+// The ascending list of rows with tau > tau_act (opacity > 1/255) in three
+// passes: per-block counts of kActRows rows, one CTA turning them into
+// offsets (exclusive scan, carried across chunks of kThreads blocks) plus the
+// total, and the ordered write (warp ballots, then warps and row groups in
+// row order).
+constexpr int kActRpt = 4;
+constexpr int kActRows = kThreads * kActRpt;
+
+__global__ void active_count_kernel(const float *__restrict__ tau, int32_t n, float tau_act, int32_t *blk)
+{
+    __shared__ int32_t warp_sum[kThreads / 32];
+    const int64_t r0 = (int64_t)blockIdx.x * kActRows;
+    int c = 0;
+#pragma unroll
+    for (int j = 0; j < kActRpt; ++j) {
+        const int64_t r = r0 + j * kThreads + threadIdx.x;
+        c += (r < n && __ldcs(tau + r) > tau_act) ? 1 : 0;
+    }
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int s = 0;
+        for (int w = 0; w < kThreads / 32; ++w) s += warp_sum[w];
+        blk[blockIdx.x] = s;
+    }
+}
+
+__global__ void active_scan_kernel(int32_t *blk, int32_t nblk, long long *total)
+{
+    __shared__ int32_t warp_sum[kThreads / 32];
+    __shared__ int32_t carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nblk; base += kThreads) {
+        const int i = base + threadIdx.x;
+        const int x = i < nblk ? blk[i] : 0;
+        int incl = x;                                   // inclusive scan within the warp
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += y;
+        }
+        if (lane == 31) warp_sum[warp] = incl;
+        __syncthreads();
+        int before = carry;
+        for (int w = 0; w < warp; ++w) before += warp_sum[w];
+        if (i < nblk) blk[i] = before + incl - x;       // exclusive offset of block i
+        __syncthreads();
+        if (threadIdx.x == kThreads - 1) carry = before + incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void active_write_kernel(const float *__restrict__ tau, int32_t n, float tau_act,
+                                    const int32_t *__restrict__ off, int32_t *__restrict__ rows)
+{
+    constexpr int kWarps = kThreads / 32;
+    __shared__ int32_t cnt[kActRpt * kWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t r0 = (int64_t)blockIdx.x * kActRows;
+    unsigned bal[kActRpt];
+#pragma unroll
+    for (int j = 0; j < kActRpt; ++j) {
+        const int64_t r = r0 + j * kThreads + threadIdx.x;
+        bal[j] = __ballot_sync(0xffffffffu, r < n && tau[r] > tau_act);
+        if (lane == 0) cnt[j * kWarps + warp] = __popc(bal[j]);
+    }
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+    int base = off[blockIdx.x];
+#pragma unroll
+    for (int j = 0; j < kActRpt; ++j) {
+        const int me = j * kWarps + warp;
+        int b = base;
+        for (int q = 0; q < me; ++q) b += cnt[q];
+        if (bal[j] & (1u << lane)) rows[b + __popc(bal[j] & lt)] = (int32_t)(r0 + j * kThreads + threadIdx.x);
+    }
+}
+
 unsigned blocks_for(int64_t n_threads) { return (unsigned)((n_threads + kThreads - 1) / kThreads); }
 
 }  // namespace
@@ -282,6 +367,19 @@ cudaError_t launch_gather_attrs(const gs_attrs &in, int32_t n_in, const gs_attrs
 {
     if (n_new <= 0) return cudaSuccess;
     gather_attrs_kernel<<<blocks_for((int64_t)n_new * kGatherLanes), kThreads, 0, s>>>(in, n_in, out, src, n_new, err);
+    return cudaGetLastError();
+}
+
+int64_t active_rows_scratch(int64_t n) { return std::max<int64_t>(1, (n + kActRows - 1) / kActRows); }
+
+cudaError_t launch_active_rows(const float *tau, int32_t n, float tau_act, int32_t *blk, int32_t *rows,
+                               long long *n_active, cudaStream_t s)
+{
+    if (n <= 0) return cudaMemsetAsync(n_active, 0, sizeof(long long), s);
+    const int32_t nblk = (int32_t)((n + kActRows - 1) / kActRows);
+    active_count_kernel<<<nblk, kThreads, 0, s>>>(tau, n, tau_act, blk);
+    active_scan_kernel<<<1, kThreads, 0, s>>>(blk, nblk, n_active);
+    if (rows) active_write_kernel<<<nblk, kThreads, 0, s>>>(tau, n, tau_act, blk, rows);
     return cudaGetLastError();
 }
 

@@ -74,8 +74,17 @@ struct StepArgs {
     int32_t dar_o, dar_s, restate, bias_mode, reg_mode;
     uint32_t k_bias;             // step used for bias correction when bias_mode == 1
     uint64_t seed;
-    uint64_t k_ctr;              // StSS counter high word (the iteration k)
+    uint64_t k_ctr;              // iteration k: bits 32-61 of every draw counter
     uint64_t rs_thr;             // row sampled iff (draw >> 11) < rs_thr
+    // position noise (App. Eq. disentangled_mu), AIU (Sec. 3.2), active count
+    int32_t noise;               // gs_noise_mode
+    int32_t aiu;                 // AIU on this step
+    float noise_scale;           // eta_Ro * lr[0]
+    float noise_k, noise_t;      // lambda_mu, lambda_t
+    float aiu_scale;             // eta_AIU
+    float tau_act;               // active iff tau > tau_act (largest float below -ln 254)
+    uint64_t aiu_thr;            // AIU-sampled iff (draw >> 11) < aiu_thr
+    unsigned long long *n_active;   // optional, accumulated with atomicAdd
 };
 
 // ------------------------------------------------------- device helpers
@@ -102,11 +111,25 @@ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t counte
     return z ^ (z >> 31);
 }
 
+// Counter of a draw: the use in bits 62-63 (0 StSS, 1 AIU, 2-3 noise), the
+// iteration in bits 32-61, the row in bits 0-31.
+__device__ __forceinline__ uint64_t draw_counter(uint64_t tag, uint64_t k, int32_t row)
+{
+    return (tag << 62) | (k << 32) | (uint64_t)(uint32_t)row;
+}
+
 // StSS membership of `row` at the sampling event a.k_ctr.
 __device__ __forceinline__ bool stss_sampled(const StepArgs &a, int32_t row)
 {
-    const uint64_t h = splitmix64_at(a.seed, (a.k_ctr << 32) | (uint64_t)(uint32_t)row);
+    const uint64_t h = splitmix64_at(a.seed, draw_counter(0, a.k_ctr, row));
     return (h >> 11) < a.rs_thr;
+}
+
+// AIU membership of an invisible `row` (Sec. 3.2: a uniform sampler).
+__device__ __forceinline__ bool aiu_sampled(const StepArgs &a, int32_t row)
+{
+    const uint64_t h = splitmix64_at(a.seed, draw_counter(1, a.k_ctr, row));
+    return (h >> 11) < a.aiu_thr;
 }
 
 // Derivative of the L1 regulariser through the opacity activation,
@@ -157,6 +180,8 @@ struct BatchParams {
 // (defined in the kernel translation units, called by api.cu)
 
 cudaError_t launch_step(const StepArgs &a, int prec, int vis_src, cudaStream_t s);
+// the step with position noise, AIU or the active count (launch_step forwards to it)
+cudaError_t launch_step_ext(const StepArgs &a, int prec, int vis_src, cudaStream_t s);
 // Batched launch with candidate configuration `cand` (0 .. batch_candidates-1)
 // over the device scene table p (tile_start built for that candidate's tile
 // size, see batch_candidate_info); *grid receives the persistent grid.  With
@@ -165,6 +190,9 @@ int batch_candidates(int prec);
 void batch_candidate_info(int prec, int cand, int *tile, int *width, int *min_blocks);
 cudaError_t launch_batch(const BatchParams *p, unsigned *work, unsigned *done, int prec, int cand, cudaStream_t s,
                          int *grid, void **fn);
+cudaError_t launch_active_rows(const float *tau, int32_t n, float tau_act, int32_t *blk, int32_t *rows,
+                               long long *n_active, cudaStream_t s);
+int64_t active_rows_scratch(int64_t n);     // int32 entries of scratch launch_active_rows needs
 cudaError_t launch_visibility(const float *xyz, int32_t n, const float cam[16], uint8_t *mask,
                               int32_t *list, unsigned long long *count, cudaStream_t s);
 cudaError_t launch_bias_table(double beta1, double beta2, int32_t len, double *t1, double *t2,

@@ -1,0 +1,410 @@
+// Device pieces shared by the step kernels (step_kernels.cu) and the
+// extended step (step_ext.cu): load/store helpers, the moment storage
+// formats State<kPrec>, and the per-row work items of a visible row and
+// of an invisible StSS-sampled row.  Every function is inline and file-local
+// to the translation unit that includes it.
+#pragma once
+
+#include <algorithm>
+
+#include "gs_internal.cuh"
+
+namespace gs {
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ float4 ldg4_stream(const float *p)
+{
+    return __ldcs(reinterpret_cast<const float4 *>(p));
+}
+// results are not read again in this step: store them evict-first
+__device__ __forceinline__ void st4(float *p, float4 x) { __stcs(reinterpret_cast<float4 *>(p), x); }
+
+__device__ __forceinline__ void unpack_bf16x2(uint32_t u, float &x, float &y)
+{
+    const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u));
+    x = f.x;
+    y = f.y;
+}
+__device__ __forceinline__ uint32_t pack_bf16x2(float x, float y)
+{
+    const __nv_bfloat162 p = __floats2bfloat162_rn(x, y);
+    return *reinterpret_cast<const uint32_t *>(&p);
+}
+
+// MurmurHash3's 32-bit finaliser (Appleby, public domain): the random bits of
+// stochastic rounding, a function of (seed, iteration, row, column) only.
+__device__ __forceinline__ uint32_t fmix32(uint32_t h)
+{
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
+// FP32 -> BF16 bits rounded stochastically: add 16 random bits below the kept
+// mantissa and truncate (rounds up with probability equal to the discarded
+// fraction, so the rounding is unbiased).  Inf / NaN round to nearest.
+__device__ __forceinline__ uint32_t bf16_bits_sr(float x, uint32_t rnd16)
+{
+    const uint32_t u = __float_as_uint(x);
+    if ((u & 0x7f800000u) == 0x7f800000u) return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+    return (u + (rnd16 & 0xffffu)) >> 16;
+}
+__device__ __forceinline__ uint32_t pack_bf16x2_sr(float x, float y, uint32_t h)
+{
+    return bf16_bits_sr(x, h) | (bf16_bits_sr(y, h >> 16) << 16);
+}
+
+// ------------------------------------------------------------ state formats
+// A small chunk (small item c = 12, 13, 14): 4 moments of m and of v as FP32,
+// plus t where the format keeps it in chunk 14.
+struct Chunk {
+    float4 m, v;
+    uint32_t t;
+};
+
+// Every format provides
+//   kRowBytes, kTByte   row size and byte offset of t in the m row
+//   kTInSh              t is carried by SH item 0 (else by small chunk 14)
+//   load_sh / store_sh  the moments of SH columns kW*i .. kW*i+kW-1 (+ t)
+//   load_small / store_small  small chunk c in 12..14 (rotation; xyz +
+//                       scale0; scale1, scale2, opacity, [t or unused])
+template <int kPrec>
+struct State;
+
+template <>
+struct State<GS_MOM_FP32> {
+    static constexpr int kRowBytes = kRowBytesF32, kTByte = kTByteF32;
+    static constexpr bool kTInSh = false;
+    static __device__ __forceinline__ float *row(void *base, int32_t r)
+    {
+        return static_cast<float *>(base) + (size_t)r * kSlots;
+    }
+    template <int kW>
+    static __device__ __forceinline__ void load_sh(const StepArgs &a, int32_t r, int i, float *m, float *v, uint32_t &)
+    {
+#pragma unroll
+        for (int q = 0; q < kW / 4; ++q) {
+            const float4 x = ld4(row(a.m, r) + kW * i + 4 * q), y = ld4(row(a.v, r) + kW * i + 4 * q);
+            m[4 * q] = x.x; m[4 * q + 1] = x.y; m[4 * q + 2] = x.z; m[4 * q + 3] = x.w;
+            v[4 * q] = y.x; v[4 * q + 1] = y.y; v[4 * q + 2] = y.z; v[4 * q + 3] = y.w;
+        }
+    }
+    template <int kW>
+    static __device__ __forceinline__ void store_sh(const StepArgs &a, int32_t r, int i, const float *m,
+                                                    const float *v, uint32_t)
+    {
+#pragma unroll
+        for (int q = 0; q < kW / 4; ++q) {
+            st4(row(a.m, r) + kW * i + 4 * q, make_float4(m[4 * q], m[4 * q + 1], m[4 * q + 2], m[4 * q + 3]));
+            st4(row(a.v, r) + kW * i + 4 * q, make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
+        }
+    }
+    static __device__ __forceinline__ Chunk load_small(const StepArgs &a, int32_t r, int c)
+    {
+        Chunk k;
+        k.m = ld4(row(a.m, r) + 4 * c);
+        k.v = ld4(row(a.v, r) + 4 * c);
+        k.t = __float_as_uint(k.m.w);           // slot 59 of m (meaningful for c == 14)
+        return k;
+    }
+    static __device__ __forceinline__ void store_small(const StepArgs &a, int32_t r, int c, Chunk k)
+    {
+        if (c == 14) k.m.w = __uint_as_float(k.t);
+        st4(row(a.m, r) + 4 * c, k.m);
+        st4(row(a.v, r) + 4 * c, k.v);
+    }
+};
+
+// kW BF16 values at p (kW = 4: one uint2, 8: one uint4) <-> FP32
+template <int kW>
+__device__ __forceinline__ void load_bf16(const char *p, float *x)
+{
+    if (kW == 4) {
+        const uint2 u = *reinterpret_cast<const uint2 *>(p);
+        unpack_bf16x2(u.x, x[0], x[1]);
+        unpack_bf16x2(u.y, x[2], x[3]);
+    } else {
+        const uint4 u = *reinterpret_cast<const uint4 *>(p);
+        unpack_bf16x2(u.x, x[0], x[1]);
+        unpack_bf16x2(u.y, x[2], x[3]);
+        unpack_bf16x2(u.z, x[kW > 4 ? 4 : 0], x[kW > 4 ? 5 : 0]);
+        unpack_bf16x2(u.w, x[kW > 4 ? 6 : 0], x[kW > 4 ? 7 : 0]);
+    }
+}
+template <int kW>
+__device__ __forceinline__ void store_bf16_rn(char *p, const float *x)
+{
+    if (kW == 4)
+        __stcs(reinterpret_cast<uint2 *>(p), make_uint2(pack_bf16x2(x[0], x[1]), pack_bf16x2(x[2], x[3])));
+    else
+        __stcs(reinterpret_cast<uint4 *>(p),
+               make_uint4(pack_bf16x2(x[0], x[1]), pack_bf16x2(x[2], x[3]), pack_bf16x2(x[kW > 4 ? 4 : 0], x[kW > 4 ? 5 : 0]),
+                          pack_bf16x2(x[kW > 4 ? 6 : 0], x[kW > 4 ? 7 : 0])));
+}
+
+// BF16 rows of 64 slots (128 B): SH column j at byte 2j; small chunk c at byte
+// 8c; t = uint32 at byte 120, loaded and stored with chunk 14 as one 16-B
+// access (slots 56-63).
+template <>
+struct State<GS_MOM_BF16> {
+    static constexpr int kRowBytes = kRowBytesBf16, kTByte = kTByteBf16;
+    static constexpr bool kTInSh = false;
+    static __device__ __forceinline__ char *row(void *base, int32_t r)
+    {
+        return static_cast<char *>(base) + (size_t)r * kRowBytes;
+    }
+    template <int kW>
+    static __device__ __forceinline__ void load_sh(const StepArgs &a, int32_t r, int i, float *m, float *v, uint32_t &)
+    {
+        load_bf16<kW>(row(a.m, r) + 2 * kW * i, m);
+        load_bf16<kW>(row(a.v, r) + 2 * kW * i, v);
+    }
+    template <int kW>
+    static __device__ __forceinline__ void store_sh(const StepArgs &a, int32_t r, int i, const float *m,
+                                                    const float *v, uint32_t)
+    {
+        store_bf16_rn<kW>(row(a.m, r) + 2 * kW * i, m);
+        store_bf16_rn<kW>(row(a.v, r) + 2 * kW * i, v);
+    }
+    static __device__ __forceinline__ Chunk load_small(const StepArgs &a, int32_t r, int c)
+    {
+        Chunk k;
+        float x[4];
+        if (c < 14) {
+            load_bf16<4>(row(a.m, r) + 8 * c, x);
+            k.t = 0;
+        } else {
+            const uint4 um = *reinterpret_cast<const uint4 *>(row(a.m, r) + 112);
+            unpack_bf16x2(um.x, x[0], x[1]);
+            unpack_bf16x2(um.y, x[2], x[3]);
+            k.t = um.z;
+        }
+        k.m = make_float4(x[0], x[1], x[2], x[3]);
+        load_bf16<4>(row(a.v, r) + 8 * c, x);
+        k.v = make_float4(x[0], x[1], x[2], x[3]);
+        return k;
+    }
+    static __device__ __forceinline__ void store_small(const StepArgs &a, int32_t r, int c, const Chunk &k)
+    {
+        if (c < 14) {
+            __stcs(reinterpret_cast<uint2 *>(row(a.m, r) + 8 * c),
+                   make_uint2(pack_bf16x2(k.m.x, k.m.y), pack_bf16x2(k.m.z, k.m.w)));
+        } else {
+            __stcs(reinterpret_cast<uint4 *>(row(a.m, r) + 112),
+                   make_uint4(pack_bf16x2(k.m.x, k.m.y), pack_bf16x2(k.m.z, k.m.w), k.t, 0u));
+        }
+        __stcs(reinterpret_cast<uint2 *>(row(a.v, r) + 8 * c),
+               make_uint2(pack_bf16x2(k.v.x, k.v.y), pack_bf16x2(k.v.z, k.v.w)));
+    }
+};
+
+// BF16 hybrid rows (160 B): FP32 part of 16 slots — [0-2] SH DC, [3] t,
+// [4-7] rotation, [8-10] xyz, [11-13] scale, [14] opacity — then the 48 SH
+// columns as BF16 at byte 64 (slots 0-2 unused).  SH item 0 takes the DC
+// moments and t from the FP32 part.  m is rounded to nearest; v is rounded
+// stochastically: its ~0.1 % per-step EMA increment is below BF16 resolution,
+// and round-to-nearest would freeze it.
+template <>
+struct State<GS_MOM_BF16_HYBRID> {
+    static constexpr int kRowBytes = kRowBytesHyb, kTByte = kTByteHyb;
+    static constexpr bool kTInSh = true;
+    static __device__ __forceinline__ char *row(void *base, int32_t r)
+    {
+        return static_cast<char *>(base) + (size_t)r * kRowBytes;
+    }
+    template <int kW>
+    static __device__ __forceinline__ void load_sh(const StepArgs &a, int32_t r, int i, float *m, float *v,
+                                                   uint32_t &t)
+    {
+        load_bf16<kW>(row(a.m, r) + kHybShByte + 2 * kW * i, m);
+        load_bf16<kW>(row(a.v, r) + kHybShByte + 2 * kW * i, v);
+        if (i == 0) {
+            const float4 fm = *reinterpret_cast<const float4 *>(row(a.m, r));
+            const float4 fv = *reinterpret_cast<const float4 *>(row(a.v, r));
+            m[0] = fm.x; m[1] = fm.y; m[2] = fm.z;
+            v[0] = fv.x; v[1] = fv.y; v[2] = fv.z;
+            t = __float_as_uint(fm.w);
+        }
+    }
+    template <int kW>
+    static __device__ __forceinline__ void store_sh(const StepArgs &a, int32_t r, int i, const float *m,
+                                                    const float *v, uint32_t t)
+    {
+        float mm[kW], vv[kW];
+#pragma unroll
+        for (int e = 0; e < kW; ++e) {
+            mm[e] = m[e];
+            vv[e] = v[e];
+        }
+        if (i == 0) {
+            st4(reinterpret_cast<float *>(row(a.m, r)), make_float4(m[0], m[1], m[2], __uint_as_float(t)));
+            st4(reinterpret_cast<float *>(row(a.v, r)), make_float4(v[0], v[1], v[2], 0.f));
+            mm[0] = mm[1] = mm[2] = vv[0] = vv[1] = vv[2] = 0.f;   // BF16 DC slots are unused
+        }
+        store_bf16_rn<kW>(row(a.m, r) + kHybShByte + 2 * kW * i, mm);
+        uint32_t w[kW / 2];
+#pragma unroll
+        for (int q = 0; q < kW / 2; q += 2) {
+            const uint32_t h = fmix32((uint32_t)r * 0x9e3779b1u ^ (uint32_t)(kW * i + 2 * q) * 0x85ebca77u ^
+                                      (uint32_t)a.k_ctr * 0xc2b2ae3du ^ (uint32_t)a.seed);
+            const uint32_t h2 = fmix32(h ^ 0x27d4eb2fu);
+            w[q] = pack_bf16x2_sr(vv[2 * q], vv[2 * q + 1], h);
+            w[q + 1] = pack_bf16x2_sr(vv[2 * q + 2], vv[2 * q + 3], h2);
+        }
+        char *pv = row(a.v, r) + kHybShByte + 2 * kW * i;
+        if (kW == 4)
+            __stcs(reinterpret_cast<uint2 *>(pv), make_uint2(w[0], w[1]));
+        else
+            __stcs(reinterpret_cast<uint4 *>(pv), make_uint4(w[0], w[1], w[kW > 4 ? 2 : 0], w[kW > 4 ? 3 : 0]));
+    }
+    static __device__ __forceinline__ Chunk load_small(const StepArgs &a, int32_t r, int c)
+    {
+        Chunk k;
+        k.m = *reinterpret_cast<const float4 *>(row(a.m, r) + 16 * (c - 11));
+        k.v = *reinterpret_cast<const float4 *>(row(a.v, r) + 16 * (c - 11));
+        k.t = 0;
+        return k;
+    }
+    static __device__ __forceinline__ void store_small(const StepArgs &a, int32_t r, int c, const Chunk &k)
+    {
+        st4(reinterpret_cast<float *>(row(a.m, r) + 16 * (c - 11)), k.m);
+        st4(reinterpret_cast<float *>(row(a.v, r) + 16 * (c - 11)), k.v);
+    }
+};
+
+// ---------------------------------------------------------------- the items
+
+// SH item i of a visible row: SH columns kW*i .. kW*i+kW-1 (0-2 are the DC
+// term, learning rate lr[4]; the rest lr[5]); no regulariser.
+template <int kPrec, int kW>
+__device__ __forceinline__ void sh_item(const StepArgs &a, const int32_t row, const int i, const bool sampled,
+                                        const float2 f)
+{
+    using S = State<kPrec>;
+    float m[kW], v[kW], th[kW], g[kW];
+    uint32_t t = 0;
+    S::template load_sh<kW>(a, row, i, m, v, t);
+    const size_t off = (size_t)row * 48 + kW * i;
+#pragma unroll
+    for (int q = 0; q < kW / 4; ++q) {
+        const float4 x = ld4(a.a_sh + off + 4 * q), y = ldg4_stream(a.g_sh + off + 4 * q);
+        th[4 * q] = x.x; th[4 * q + 1] = x.y; th[4 * q + 2] = x.z; th[4 * q + 3] = x.w;
+        g[4 * q] = y.x; g[4 * q + 1] = y.y; g[4 * q + 2] = y.z; g[4 * q + 3] = y.w;
+    }
+#pragma unroll
+    for (int e = 0; e < kW; ++e) {
+        const float lr = (i == 0 && e < 3) ? a.lr[4] : a.lr[5];
+        th[e] = step_element(th[e], g[e], m[e], v[e], f.x, f.y, a, lr, false, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int q = 0; q < kW / 4; ++q)
+        st4(a.a_sh + off + 4 * q, make_float4(th[4 * q], th[4 * q + 1], th[4 * q + 2], th[4 * q + 3]));
+    if (S::kTInSh && i == 0) t += 1u;      // the row's own step count (Sec. 3.2)
+    if (sampled) {                         // RSR post-scale (Eq. meth::restate)
+#pragma unroll
+        for (int e = 0; e < kW; ++e) {
+            m[e] *= a.alpha1;
+            v[e] *= a.alpha2;
+        }
+    }
+    S::template store_sh<kW>(a, row, i, m, v, t);
+}
+
+// Small item c of a visible row: 12 rotation, 13 xyz + scale0, 14 scale1 +
+// scale2 + opacity (+ t where the format keeps it there).
+template <int kPrec>
+__device__ __forceinline__ void small_item(const StepArgs &a, const int32_t row, const int c, const bool sampled,
+                                           const float2 f)
+{
+    using S = State<kPrec>;
+    Chunk k = S::load_small(a, row, c);
+    float4 &m = k.m, &v = k.v;
+    const size_t r = (size_t)row;
+    if (c == 12) {
+        // rotation quaternion
+        float *pt = a.a_rot + r * 4;
+        float4 th = ld4(pt);
+        const float4 g = ldg4_stream(a.g_rot + r * 4);
+        const float l = a.lr[2];
+        th.x = step_element(th.x, g.x, m.x, v.x, f.x, f.y, a, l, false, 0.f, 0.f, 0.f);
+        th.y = step_element(th.y, g.y, m.y, v.y, f.x, f.y, a, l, false, 0.f, 0.f, 0.f);
+        th.z = step_element(th.z, g.z, m.z, v.z, f.x, f.y, a, l, false, 0.f, 0.f, 0.f);
+        th.w = step_element(th.w, g.w, m.w, v.w, f.x, f.y, a, l, false, 0.f, 0.f, 0.f);
+        st4(pt, th);
+    } else if (c == 13) {
+        // xyz and the first log-scale component
+        float *px = a.a_xyz + r * 3;
+        float *ps = a.a_scale + r * 3;
+        const float *gx = a.g_xyz + r * 3;
+        float x0 = px[0], x1 = px[1], x2 = px[2], s0 = ps[0];
+        const float g0 = __ldcs(gx), g1 = __ldcs(gx + 1), g2 = __ldcs(gx + 2), gs0 = __ldcs(a.g_scale + r * 3);
+        const bool ds = a.dar_s != 0;
+        // scale: dR/dkappa = exp(kappa) at the old value (App. Eq. scale)
+        const float r0s = ds ? expf(s0) : 0.f;
+        x0 = step_element(x0, g0, m.x, v.x, f.x, f.y, a, a.lr[0], false, 0.f, 0.f, 0.f);
+        x1 = step_element(x1, g1, m.y, v.y, f.x, f.y, a, a.lr[0], false, 0.f, 0.f, 0.f);
+        x2 = step_element(x2, g2, m.z, v.z, f.x, f.y, a, a.lr[0], false, 0.f, 0.f, 0.f);
+        s0 = step_element(s0, gs0, m.w, v.w, f.x, f.y, a, a.lr[1], ds, r0s, a.lam_s, a.clip_s);
+        __stcs(px, x0); __stcs(px + 1, x1); __stcs(px + 2, x2);
+        __stcs(ps, s0);
+    } else {
+        // the other two log-scale components and the opacity logit
+        float *ps = a.a_scale + r * 3;
+        float *po = a.a_op + r;
+        const float *gsp = a.g_scale + r * 3;
+        float s1 = ps[1], s2 = ps[2], op = *po;
+        const float gs1 = __ldcs(gsp + 1), gs2 = __ldcs(gsp + 2), go = __ldcs(a.g_op + r);
+        const bool ds = a.dar_s != 0, dop = a.dar_o != 0;
+        const float r1s = ds ? expf(s1) : 0.f, r2s = ds ? expf(s2) : 0.f;
+        // opacity: dR/dtau = sig'(tau) at the old value (App. Eq. opacity)
+        const float rop = dop ? dsigmoid(op) : 0.f;
+        s1 = step_element(s1, gs1, m.x, v.x, f.x, f.y, a, a.lr[1], ds, r1s, a.lam_s, a.clip_s);
+        s2 = step_element(s2, gs2, m.y, v.y, f.x, f.y, a, a.lr[1], ds, r2s, a.lam_s, a.clip_s);
+        op = step_element(op, go, m.z, v.z, f.x, f.y, a, a.lr[3], dop, rop, a.lam_o, a.clip_o);
+        __stcs(ps + 1, s1); __stcs(ps + 2, s2);
+        __stcs(po, op);
+        if (!S::kTInSh) k.t += 1u;         // the row's own step count (Sec. 3.2)
+    }
+    if (sampled) {         // RSR post-scale (chunk 14 holds 3 moments)
+        m.x *= a.alpha1; m.y *= a.alpha1; m.z *= a.alpha1;
+        v.x *= a.alpha2; v.y *= a.alpha2; v.z *= a.alpha2;
+        if (c != 14) { m.w *= a.alpha1; v.w *= a.alpha2; }
+    }
+    S::store_small(a, row, c, k);
+}
+
+// RSR (Eq. meth::restate) of an invisible StSS-sampled row: SH item i
+// (i < 48/kW) or small chunk c = 12 + (i - 48/kW); t is left unchanged.
+template <int kPrec, int kW>
+__device__ __forceinline__ void rsr_item(const StepArgs &a, const int32_t row, const int i)
+{
+    using S = State<kPrec>;
+    constexpr int kNsh = 48 / kW;
+    if (i < kNsh) {
+        float m[kW], v[kW];
+        uint32_t t = 0;
+        S::template load_sh<kW>(a, row, i, m, v, t);
+#pragma unroll
+        for (int e = 0; e < kW; ++e) {
+            m[e] *= a.alpha1;
+            v[e] *= a.alpha2;
+        }
+        S::template store_sh<kW>(a, row, i, m, v, t);
+    } else {
+        const int c = 12 + (i - kNsh);
+        Chunk k = S::load_small(a, row, c);
+        k.m.x *= a.alpha1; k.m.y *= a.alpha1; k.m.z *= a.alpha1;
+        k.v.x *= a.alpha2; k.v.y *= a.alpha2; k.v.z *= a.alpha2;
+        if (c != 14) { k.m.w *= a.alpha1; k.v.w *= a.alpha2; }
+        S::store_small(a, row, c, k);
+    }
+}
+
+}  // namespace
+}  // namespace gs

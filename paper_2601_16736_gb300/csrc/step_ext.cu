@@ -1,0 +1,371 @@
+// The step with its optional terms: position noise (App. Eq.
+// disentangled_mu), the Artificial Implicit Update of sampled invisible
+// primitives (Sec. 3.2), and the active count N_a (Sec. 4, opacity > 1/255).
+// Launched only when a step asks for one of them; the plain step kernel is
+// untouched by them.
+//
+// Per tile of 256 rows (one CTA of 256 threads):
+//   A. visibility, StSS, AIU and noise decisions per row; three
+//      shared-memory lists: visible rows, invisible rows with RSR and/or AIU,
+//      invisible rows with the noise only.  Rows no item will touch are
+//      counted for N_a here (their opacity is unchanged).
+//   B. items: the SH items of visible rows (as in the plain step), one row
+//      item per visible row for its 11 small columns; SH items and a row item
+//      per RSR/AIU row; a noise item per noise-only row.  A row item reads the
+//      rotation, scale and opacity before it updates any of them, so the noise
+//      of that row sees its values before this step.
+
+#include "step_common.cuh"
+
+namespace gs {
+namespace {
+
+constexpr uint8_t kFRsr = 1, kFAiu = 2, kFNoise = 4;
+
+// gamma ~ N(0, I_3) by the Box-Muller transform (Box & Muller 1958) on
+// 24-bit uniforms from two SplitMix64 words (stream tags 2 and 3):
+// ua = (w >> 40 + 1) / 2^24 in (0, 1], ub = bits 16..39 / 2^24 in [0, 1).
+__device__ __forceinline__ float3 noise_gamma(const StepArgs &a, int32_t row)
+{
+    const uint64_t h1 = splitmix64_at(a.seed, draw_counter(2, a.k_ctr, row));
+    const uint64_t h2 = splitmix64_at(a.seed, draw_counter(3, a.k_ctr, row));
+    const float ua1 = (float)((h1 >> 40) + 1ull) * 0x1p-24f, ub1 = (float)((h1 >> 16) & 0xFFFFFFull) * 0x1p-24f;
+    const float ua2 = (float)((h2 >> 40) + 1ull) * 0x1p-24f, ub2 = (float)((h2 >> 16) & 0xFFFFFFull) * 0x1p-24f;
+    const float r1 = sqrtf(-2.f * logf(ua1)), r2 = sqrtf(-2.f * logf(ua2));
+    float s1, c1;
+    sincospif(2.f * ub1, &s1, &c1);
+    return make_float3(r1 * c1, r1 * s1, r2 * cospif(2.f * ub2));
+}
+
+// Position noise of one primitive from its values before this step (App.
+// Eq. disentangled_mu): the amount subtracted from mu,
+//   eta_Ro * eta_mu * sigmoid(-lambda_mu (o - lambda_t)) * Sigma gamma,
+// Sigma = R diag(exp(2 kappa)) R^T, R the rotation of the normalised
+// quaternion q = (w, x, y, z).  Sigma gamma is formed as R (s^2 .* (R^T gamma)).
+__device__ __forceinline__ float3 noise_term(const StepArgs &a, int32_t row, float4 q, float k0, float k1, float k2,
+                                             float tau)
+{
+    const float o = 1.f / (1.f + expf(-tau));
+    const float gate = 1.f / (1.f + expf(a.noise_k * (o - a.noise_t)));
+    const float c = a.noise_scale * gate;
+    if (c == 0.f) return make_float3(0.f, 0.f, 0.f);
+    const float3 g = noise_gamma(a, row);
+    const float nrm = fmaxf(sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w), 1e-12f);
+    const float w = q.x / nrm, x = q.y / nrm, y = q.z / nrm, z = q.w / nrm;
+    const float r00 = 1.f - 2.f * (y * y + z * z), r01 = 2.f * (x * y - w * z), r02 = 2.f * (x * z + w * y);
+    const float r10 = 2.f * (x * y + w * z), r11 = 1.f - 2.f * (x * x + z * z), r12 = 2.f * (y * z - w * x);
+    const float r20 = 2.f * (x * z - w * y), r21 = 2.f * (y * z + w * x), r22 = 1.f - 2.f * (x * x + y * y);
+    const float p0 = (r00 * g.x + r10 * g.y + r20 * g.z) * expf(2.f * k0);
+    const float p1 = (r01 * g.x + r11 * g.y + r21 * g.z) * expf(2.f * k1);
+    const float p2 = (r02 * g.x + r12 * g.y + r22 * g.z) * expf(2.f * k2);
+    return make_float3(c * (r00 * p0 + r01 * p1 + r02 * p2), c * (r10 * p0 + r11 * p1 + r12 * p2),
+                       c * (r20 * p0 + r21 * p1 + r22 * p2));
+}
+
+// The AIU step of one value from unchanged moments: theta - lr m^/(sqrt(v^) + eps).
+__device__ __forceinline__ float aiu_element(float th, float m, float v, float2 f, float eps, float lr)
+{
+    return fmaf(-lr, (m * f.x) / fmaf(sqrtf(v), f.y, eps), th);
+}
+
+// SH item i of an invisible row with RSR and/or AIU: the AIU step of its
+// attributes from the current moments, then the RSR scaling of the moments.
+template <int kPrec, int kW>
+__device__ __forceinline__ void inv_sh_item(const StepArgs &a, const int32_t row, const int i, const uint8_t fl,
+                                            const float2 f)
+{
+    using S = State<kPrec>;
+    float m[kW], v[kW];
+    uint32_t t = 0;
+    S::template load_sh<kW>(a, row, i, m, v, t);
+    if (fl & kFAiu) {
+        const size_t off = (size_t)row * 48 + kW * i;
+#pragma unroll
+        for (int q = 0; q < kW / 4; ++q) {
+            float4 x = ld4(a.a_sh + off + 4 * q);
+            const int e0 = 4 * q;
+            const float l0 = ((i == 0 && e0 + 0 < 3) ? a.lr[4] : a.lr[5]) * a.aiu_scale;
+            const float l1 = ((i == 0 && e0 + 1 < 3) ? a.lr[4] : a.lr[5]) * a.aiu_scale;
+            const float l2 = ((i == 0 && e0 + 2 < 3) ? a.lr[4] : a.lr[5]) * a.aiu_scale;
+            const float l3 = a.lr[5] * a.aiu_scale;
+            x.x = aiu_element(x.x, m[e0], v[e0], f, a.eps, l0);
+            x.y = aiu_element(x.y, m[e0 + 1], v[e0 + 1], f, a.eps, l1);
+            x.z = aiu_element(x.z, m[e0 + 2], v[e0 + 2], f, a.eps, l2);
+            x.w = aiu_element(x.w, m[e0 + 3], v[e0 + 3], f, a.eps, l3);
+            st4(a.a_sh + off + 4 * q, x);
+        }
+    }
+    if (fl & kFRsr) {
+#pragma unroll
+        for (int e = 0; e < kW; ++e) {
+            m[e] *= a.alpha1;
+            v[e] *= a.alpha2;
+        }
+        S::template store_sh<kW>(a, row, i, m, v, t);
+    }
+}
+
+// The 11 small columns (rotation, xyz, scale, opacity) of one row in one
+// item.  vis: Sparse Adam + DAR with this step's gradient and t += 1;
+// otherwise kFAiu: the AIU step from the current moments.  kFRsr scales the
+// moments afterwards, kFNoise subtracts the position noise of the values
+// read at entry.  Returns whether the row is active after the step.
+template <int kPrec>
+__device__ __forceinline__ bool row_item(const StepArgs &a, const int32_t row, const bool vis, const uint8_t fl,
+                                         const float2 f)
+{
+    using S = State<kPrec>;
+    const size_t r = (size_t)row;
+    float *px = a.a_xyz + r * 3, *ps = a.a_scale + r * 3, *pq = a.a_rot + r * 4, *po = a.a_op + r;
+    float4 q = ld4(pq);
+    float x0 = px[0], x1 = px[1], x2 = px[2];
+    float k0 = ps[0], k1 = ps[1], k2 = ps[2];
+    float tau = *po;
+    const float3 nz = (fl & kFNoise) ? noise_term(a, row, q, k0, k1, k2, tau) : make_float3(0.f, 0.f, 0.f);
+    const bool aiu = !vis && (fl & kFAiu);
+    if (vis || aiu || (fl & kFRsr)) {
+        Chunk c12 = S::load_small(a, row, 12), c13 = S::load_small(a, row, 13), c14 = S::load_small(a, row, 14);
+        if (vis) {
+            const float4 gq = ldg4_stream(a.g_rot + r * 4);
+            const float *gx = a.g_xyz + r * 3, *gs = a.g_scale + r * 3;
+            const float g0 = __ldcs(gx), g1 = __ldcs(gx + 1), g2 = __ldcs(gx + 2);
+            const float gs0 = __ldcs(gs), gs1 = __ldcs(gs + 1), gs2 = __ldcs(gs + 2), go = __ldcs(a.g_op + r);
+            const bool ds = a.dar_s != 0, dop = a.dar_o != 0;
+            // regulariser derivatives at the old values (App. Eqs. scale, opacity)
+            const float rs0 = ds ? expf(k0) : 0.f, rs1 = ds ? expf(k1) : 0.f, rs2 = ds ? expf(k2) : 0.f;
+            const float rop = dop ? dsigmoid(tau) : 0.f;
+            q.x = step_element(q.x, gq.x, c12.m.x, c12.v.x, f.x, f.y, a, a.lr[2], false, 0.f, 0.f, 0.f);
+            q.y = step_element(q.y, gq.y, c12.m.y, c12.v.y, f.x, f.y, a, a.lr[2], false, 0.f, 0.f, 0.f);
+            q.z = step_element(q.z, gq.z, c12.m.z, c12.v.z, f.x, f.y, a, a.lr[2], false, 0.f, 0.f, 0.f);
+            q.w = step_element(q.w, gq.w, c12.m.w, c12.v.w, f.x, f.y, a, a.lr[2], false, 0.f, 0.f, 0.f);
+            x0 = step_element(x0, g0, c13.m.x, c13.v.x, f.x, f.y, a, a.lr[0], false, 0.f, 0.f, 0.f);
+            x1 = step_element(x1, g1, c13.m.y, c13.v.y, f.x, f.y, a, a.lr[0], false, 0.f, 0.f, 0.f);
+            x2 = step_element(x2, g2, c13.m.z, c13.v.z, f.x, f.y, a, a.lr[0], false, 0.f, 0.f, 0.f);
+            k0 = step_element(k0, gs0, c13.m.w, c13.v.w, f.x, f.y, a, a.lr[1], ds, rs0, a.lam_s, a.clip_s);
+            k1 = step_element(k1, gs1, c14.m.x, c14.v.x, f.x, f.y, a, a.lr[1], ds, rs1, a.lam_s, a.clip_s);
+            k2 = step_element(k2, gs2, c14.m.y, c14.v.y, f.x, f.y, a, a.lr[1], ds, rs2, a.lam_s, a.clip_s);
+            tau = step_element(tau, go, c14.m.z, c14.v.z, f.x, f.y, a, a.lr[3], dop, rop, a.lam_o, a.clip_o);
+            if (!S::kTInSh) c14.t += 1u;       // the row's own step count (Sec. 3.2)
+        } else if (aiu) {
+            const float lq = a.lr[2] * a.aiu_scale, lx = a.lr[0] * a.aiu_scale, ls = a.lr[1] * a.aiu_scale,
+                        lo = a.lr[3] * a.aiu_scale;
+            q.x = aiu_element(q.x, c12.m.x, c12.v.x, f, a.eps, lq);
+            q.y = aiu_element(q.y, c12.m.y, c12.v.y, f, a.eps, lq);
+            q.z = aiu_element(q.z, c12.m.z, c12.v.z, f, a.eps, lq);
+            q.w = aiu_element(q.w, c12.m.w, c12.v.w, f, a.eps, lq);
+            x0 = aiu_element(x0, c13.m.x, c13.v.x, f, a.eps, lx);
+            x1 = aiu_element(x1, c13.m.y, c13.v.y, f, a.eps, lx);
+            x2 = aiu_element(x2, c13.m.z, c13.v.z, f, a.eps, lx);
+            k0 = aiu_element(k0, c13.m.w, c13.v.w, f, a.eps, ls);
+            k1 = aiu_element(k1, c14.m.x, c14.v.x, f, a.eps, ls);
+            k2 = aiu_element(k2, c14.m.y, c14.v.y, f, a.eps, ls);
+            tau = aiu_element(tau, c14.m.z, c14.v.z, f, a.eps, lo);
+        }
+        if (fl & kFRsr) {      // RSR post-scale (Eq. meth::restate); chunk 14 holds 3 moments
+            c12.m.x *= a.alpha1; c12.m.y *= a.alpha1; c12.m.z *= a.alpha1; c12.m.w *= a.alpha1;
+            c12.v.x *= a.alpha2; c12.v.y *= a.alpha2; c12.v.z *= a.alpha2; c12.v.w *= a.alpha2;
+            c13.m.x *= a.alpha1; c13.m.y *= a.alpha1; c13.m.z *= a.alpha1; c13.m.w *= a.alpha1;
+            c13.v.x *= a.alpha2; c13.v.y *= a.alpha2; c13.v.z *= a.alpha2; c13.v.w *= a.alpha2;
+            c14.m.x *= a.alpha1; c14.m.y *= a.alpha1; c14.m.z *= a.alpha1;
+            c14.v.x *= a.alpha2; c14.v.y *= a.alpha2; c14.v.z *= a.alpha2;
+        }
+        if (vis || (fl & kFRsr)) {             // an AIU step leaves the moments as they are
+            S::store_small(a, row, 12, c12);
+            S::store_small(a, row, 13, c13);
+            S::store_small(a, row, 14, c14);
+        }
+        if (vis || aiu) {
+            st4(pq, q);
+            __stcs(ps, k0); __stcs(ps + 1, k1); __stcs(ps + 2, k2);
+            __stcs(po, tau);
+        }
+    }
+    if (vis || aiu || (fl & kFNoise)) {
+        __stcs(px, x0 - nz.x);
+        __stcs(px + 1, x1 - nz.y);
+        __stcs(px + 2, x2 - nz.z);
+    }
+    return tau > a.tau_act;
+}
+
+// Shared-memory lists of one tile of the extended step.
+template <int kTile>
+struct TileListsX {
+    int32_t list[kTile];      // visible rows
+    int32_t ilist[kTile];     // invisible rows with RSR and/or AIU
+    int32_t nlist[kTile];     // invisible rows with the noise only
+    float2 fac[kTile];        // bias factors of the visible rows (count t + 1)
+    float2 ifac[kTile];       // bias factors of the AIU rows (count t)
+    uint8_t vflag[kTile];
+    uint8_t iflag[kTile];
+    int32_t cnt[3][kTile / 32];
+    unsigned active;
+};
+
+__device__ __forceinline__ float2 factors(const StepArgs &a, uint32_t k)
+{
+    return k < (uint32_t)a.fac_len ? a.fac[k] : make_float2(1.0f, 1.0f);
+}
+
+// Phase A of the extended step; returns the three list lengths.
+template <int kTile, int kRowBytes, int kTByte>
+__device__ __forceinline__ void tile_decide_x(const StepArgs &a, const int vis_src, const int64_t r0,
+                                              TileListsX<kTile> &L, int &nv, int &ni, int &nn)
+{
+    constexpr int kRpt = kTile / kThreads;
+    constexpr int kWarps = kThreads / 32;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nrow = (int)min((int64_t)kTile, (int64_t)a.n_rows - r0);
+    unsigned bal_v[kRpt], bal_i[kRpt], bal_n[kRpt];
+    uint8_t flag[kRpt];
+    uint32_t t_old[kRpt];
+    unsigned my_active = 0;
+#pragma unroll
+    for (int j = 0; j < kRpt; ++j) {
+        const int lr = j * kThreads + tid;
+        const int64_t row = r0 + lr;
+        const bool in = lr < nrow;
+        bool vis = false, in_i = false, in_n = false;
+        uint8_t fl = 0;
+        t_old[j] = 0;
+        if (in) {
+            if (vis_src == kVisCamera) {
+                const float *p = a.a_xyz + row * 3;
+                vis = frustum_visible(p[0], p[1], p[2], a.cam);
+            } else if (vis_src == kVisMask) {
+                vis = a.mask_in[row] != 0;
+            } else {
+                vis = true;
+            }
+            if (a.mask_out) a.mask_out[row] = vis ? 1 : 0;
+            if (a.restate && stss_sampled(a, (int32_t)row)) fl |= kFRsr;
+            if (a.noise == GS_NOISE_ALL || (a.noise == GS_NOISE_VISIBLE && vis)) fl |= kFNoise;
+            const bool aiu_draw = a.aiu && !vis && aiu_sampled(a, (int32_t)row);
+            if ((vis || aiu_draw) && !a.bias_mode)
+                t_old[j] = *reinterpret_cast<const uint32_t *>(static_cast<const char *>(a.m) +
+                                                               (size_t)row * kRowBytes + kTByte);
+            // a primitive never seen has no moments: its AIU step is zero
+            if (aiu_draw && (a.bias_mode || t_old[j] > 0u)) fl |= kFAiu;
+            in_i = !vis && (fl & (kFRsr | kFAiu));
+            in_n = !vis && !in_i && (fl & kFNoise);
+            if (a.n_active && !vis && !in_i) my_active += a.a_op[row] > a.tau_act ? 1u : 0u;
+        }
+        flag[j] = fl;
+        bal_v[j] = __ballot_sync(0xffffffffu, vis);
+        bal_i[j] = __ballot_sync(0xffffffffu, in_i);
+        bal_n[j] = __ballot_sync(0xffffffffu, in_n);
+        if (lane == 0) {
+            L.cnt[0][j * kWarps + warp] = __popc(bal_v[j]);
+            L.cnt[1][j * kWarps + warp] = __popc(bal_i[j]);
+            L.cnt[2][j * kWarps + warp] = __popc(bal_n[j]);
+        }
+    }
+    if (tid == 0) L.active = 0u;
+    __syncthreads();
+    if (a.n_active) {
+        my_active = __reduce_add_sync(0xffffffffu, my_active);
+        if (lane == 0 && my_active) atomicAdd(&L.active, my_active);
+    }
+    nv = ni = nn = 0;
+    for (int q = 0; q < kRpt * kWarps; ++q) {
+        nv += L.cnt[0][q];
+        ni += L.cnt[1][q];
+        nn += L.cnt[2][q];
+    }
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int j = 0; j < kRpt; ++j) {
+        const int me = j * kWarps + warp;
+        int bv = 0, bi = 0, bn = 0;
+        for (int q = 0; q < me; ++q) {
+            bv += L.cnt[0][q];
+            bi += L.cnt[1][q];
+            bn += L.cnt[2][q];
+        }
+        const int32_t row = (int32_t)(r0 + j * kThreads + tid);
+        const unsigned me_bit = 1u << lane;
+        if (bal_v[j] & me_bit) {
+            const int pos = bv + __popc(bal_v[j] & lt);
+            L.list[pos] = row;
+            L.vflag[pos] = flag[j];
+            L.fac[pos] = factors(a, a.bias_mode ? a.k_bias : t_old[j] + 1u);
+        }
+        if (bal_i[j] & me_bit) {
+            const int pos = bi + __popc(bal_i[j] & lt);
+            L.ilist[pos] = row;
+            L.iflag[pos] = flag[j];
+            L.ifac[pos] = (flag[j] & kFAiu) ? factors(a, a.bias_mode ? a.k_bias : t_old[j])
+                                            : make_float2(1.0f, 1.0f);
+        }
+        if (bal_n[j] & me_bit) L.nlist[bn + __popc(bal_n[j] & lt)] = row;
+    }
+    if (tid == 0 && a.n_visible && nv) atomicAdd(a.n_visible, (unsigned long long)nv);
+    __syncthreads();
+}
+
+template <int kTile, int kMinBlocks, int kPrec, int kW>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) step_tile_x(const StepArgs a, const int vis_src)
+{
+    static_assert(kTile % kThreads == 0, "tile must be a multiple of the block");
+    using S = State<kPrec>;
+    constexpr int kNsh = 48 / kW;
+    __shared__ TileListsX<kTile> L;
+    const int64_t r0 = (int64_t)blockIdx.x * kTile;
+    int nv, ni, nn;
+    tile_decide_x<kTile, S::kRowBytes, S::kTByte>(a, vis_src, r0, L, nv, ni, nn);
+
+    unsigned my_active = 0;
+    const int e_sh = kNsh * nv, e_vis = e_sh + nv, e_ish = e_vis + kNsh * ni, e_inv = e_ish + ni, e_all = e_inv + nn;
+    for (int w = threadIdx.x; w < e_all; w += kThreads) {
+        if (w < e_sh) {
+            const int j = w / kNsh, i = w - j * kNsh;
+            sh_item<kPrec, kW>(a, L.list[j], i, (L.vflag[j] & kFRsr) != 0, L.fac[j]);
+        } else if (w < e_vis) {
+            const int j = w - e_sh;
+            my_active += row_item<kPrec>(a, L.list[j], true, L.vflag[j], L.fac[j]) ? 1u : 0u;
+        } else if (w < e_ish) {
+            const int q = w - e_vis;
+            const int j = q / kNsh, i = q - j * kNsh;
+            inv_sh_item<kPrec, kW>(a, L.ilist[j], i, L.iflag[j], L.ifac[j]);
+        } else if (w < e_inv) {
+            const int j = w - e_ish;
+            my_active += row_item<kPrec>(a, L.ilist[j], false, L.iflag[j], L.ifac[j]) ? 1u : 0u;
+        } else {
+            const int32_t row = L.nlist[w - e_inv];
+            row_item<kPrec>(a, row, false, kFNoise, make_float2(1.0f, 1.0f));
+        }
+    }
+    if (a.n_active) {
+        my_active = __reduce_add_sync(0xffffffffu, my_active);
+        if ((threadIdx.x & 31) == 0 && my_active) atomicAdd(&L.active, my_active);
+        __syncthreads();
+        if (threadIdx.x == 0 && L.active) atomicAdd(a.n_active, (unsigned long long)L.active);
+    }
+}
+
+}  // namespace
+
+constexpr int kExtTile = 256;
+constexpr int kExtMinBlocks = 2;
+
+cudaError_t launch_step_ext(const StepArgs &a, int prec, int vis_src, cudaStream_t s)
+{
+    if (a.n_rows <= 0) return cudaSuccess;
+    const unsigned grid = (unsigned)((a.n_rows + kExtTile - 1) / kExtTile);
+    switch (prec) {
+    case GS_MOM_FP32:
+        step_tile_x<kExtTile, kExtMinBlocks, GS_MOM_FP32, 4><<<grid, kThreads, 0, s>>>(a, vis_src);
+        break;
+    case GS_MOM_BF16:
+        step_tile_x<kExtTile, kExtMinBlocks, GS_MOM_BF16, 8><<<grid, kThreads, 0, s>>>(a, vis_src);
+        break;
+    case GS_MOM_BF16_HYBRID:
+        step_tile_x<kExtTile, kExtMinBlocks, GS_MOM_BF16_HYBRID, 8><<<grid, kThreads, 0, s>>>(a, vis_src);
+        break;
+    default:
+        return cudaErrorNotSupported;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace gs

@@ -18,6 +18,7 @@ _lib = None
 GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CUDA, GS_ERR_OOM, GS_ERR_UNSUPPORTED, GS_ERR_TIMEOUT, GS_ERR_STATE = range(7)
 GS_MOM_FP32, GS_MOM_BF16, GS_MOM_FP8E4M3, GS_MOM_BF16_HYBRID = range(4)
 GS_REG_DAR, GS_REG_COUPLED, GS_REG_ADAMW, GS_REG_ADAMW_CLIP = range(4)
+GS_NOISE_OFF, GS_NOISE_VISIBLE, GS_NOISE_ALL = range(3)
 GROUPS = (("xyz", 3), ("scale", 3), ("rot", 4), ("opacity", 1), ("sh", 48))
 GS_NOALLOC_MAX_ROWS = 65536
 GS_MAX_BATCH = 64
@@ -45,7 +46,10 @@ class gs_camera(ctypes.Structure):
 class gs_step_params(ctypes.Structure):
     _fields_ = [("lr", ctypes.c_float * 6), ("dar_opacity", ctypes.c_int32), ("dar_scale", ctypes.c_int32),
                 ("restate", ctypes.c_int32), ("reserved", ctypes.c_int32), ("restate_ratio", ctypes.c_double),
-                ("seed", ctypes.c_uint64), ("iteration", ctypes.c_int64), ("n_visible", ctypes.c_int64)]
+                ("seed", ctypes.c_uint64), ("iteration", ctypes.c_int64), ("n_visible", ctypes.c_int64),
+                ("noise", ctypes.c_int32), ("aiu", ctypes.c_int32), ("noise_lr", ctypes.c_float),
+                ("noise_k", ctypes.c_float), ("noise_t", ctypes.c_float), ("aiu_prob", ctypes.c_float),
+                ("aiu_scale", ctypes.c_float), ("reserved2", ctypes.c_int32), ("n_active", ctypes.c_void_p)]
 
 
 class gs_attrs(ctypes.Structure):
@@ -82,6 +86,7 @@ def _load():
                                   ctypes.POINTER(gs_step_params), ctypes.POINTER(i64), P], ctypes.c_int),
         "gs_reindex_state": ([P, P, P, i64, P], ctypes.c_int),
         "gs_gather_attrs": ([P, ctypes.POINTER(gs_attrs), i64, ctypes.POINTER(gs_attrs), P, i64, P], ctypes.c_int),
+        "gs_active_rows": ([P, P, P, P, P], ctypes.c_int),
         "gs_opt_export_state": ([P, P, P, P, P], ctypes.c_int),
         "gs_opt_import_state": ([P, P, P, P, P], ctypes.c_int),
         "gs_bias_table_len": ([P], i64),
@@ -148,10 +153,19 @@ def make_config(beta1=0.9, beta2=0.999, eps=1e-15, lambda_o=1e-3, lambda_s=1e-5,
 
 
 def make_params(lr, iteration, dar_opacity=True, dar_scale=True, restate=False, restate_ratio=0.0, seed=0,
-                n_visible=0) -> gs_step_params:
+                n_visible=0, noise=0, noise_lr=5e5, noise_k=100.0, noise_t=0.005, aiu=False, aiu_prob=0.0,
+                aiu_scale=1.0, n_active=None) -> gs_step_params:
+    """Per-step parameters.  noise: GS_NOISE_OFF / _VISIBLE / _ALL (position
+    noise of App. Eq. disentangled_mu; noise_lr, noise_k, noise_t are
+    eta_Ro, lambda_mu, lambda_t, not given by the paper: the defaults are
+    3DGS-MCMC's).  aiu: the Artificial Implicit Update with probability
+    aiu_prob and step scale aiu_scale.  n_active: optional device int64
+    tensor that receives the active count (opacity > 1/255)."""
     return gs_step_params((ctypes.c_float * 6)(*[float(x) for x in lr]), int(bool(dar_opacity)),
                           int(bool(dar_scale)), int(bool(restate)), 0, float(restate_ratio),
-                          int(seed) & (2 ** 64 - 1), int(iteration), int(n_visible))
+                          int(seed) & (2 ** 64 - 1), int(iteration), int(n_visible), int(noise), int(bool(aiu)),
+                          float(noise_lr), float(noise_k), float(noise_t), float(aiu_prob), float(aiu_scale), 0,
+                          None if n_active is None else n_active.data_ptr())
 
 
 # ------------------------------------------------------------- entry points
@@ -220,6 +234,12 @@ def gs_gather_attrs(h, attrs_in: gs_attrs, n_in: int, attrs_out: gs_attrs, src_r
                     stream=None) -> None:
     _check(_load().gs_gather_attrs(h, ctypes.byref(attrs_in), int(n_in), ctypes.byref(attrs_out), _ptr(src_rows),
                                    int(n_new), _stream(stream)), "gs_gather_attrs")
+
+
+def gs_active_rows(h, opacity, rows, n_active, stream=None) -> None:
+    """Ascending rows with opacity > 1/255 into `rows` (optional) and their
+    count into the device int64 `n_active`."""
+    _check(_load().gs_active_rows(h, _ptr(opacity), _ptr(rows), _ptr(n_active), _stream(stream)), "gs_active_rows")
 
 
 def gs_opt_export_state(h, m=None, v=None, t=None, stream=None) -> None:

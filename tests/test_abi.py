@@ -45,8 +45,9 @@ def test_struct_layouts_match_header(tmp_path, G):
 int main(void) {
   printf("%zu %zu %zu %zu %zu\n", sizeof(gs_opt_config), sizeof(gs_camera), sizeof(gs_step_params),
          sizeof(gs_attrs), sizeof(gs_grads));
-  printf("%zu %zu %zu %zu\n", offsetof(gs_opt_config, prec), offsetof(gs_opt_config, n_pixels),
-         offsetof(gs_step_params, restate_ratio), offsetof(gs_step_params, n_visible));
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", offsetof(gs_opt_config, prec), offsetof(gs_opt_config, n_pixels),
+         offsetof(gs_step_params, restate_ratio), offsetof(gs_step_params, n_visible),
+         offsetof(gs_step_params, noise), offsetof(gs_step_params, aiu_scale), offsetof(gs_step_params, n_active));
   return 0;
 }''')
     exe = tmp_path / "layout"
@@ -56,11 +57,13 @@ int main(void) {
     assert sizes[:5] == [ctypes.sizeof(G.gs_opt_config), ctypes.sizeof(G.gs_camera), ctypes.sizeof(G.gs_step_params),
                          ctypes.sizeof(G.gs_attrs), ctypes.sizeof(G.gs_grads)]
     assert sizes[5:] == [G.gs_opt_config.prec.offset, G.gs_opt_config.n_pixels.offset,
-                         G.gs_step_params.restate_ratio.offset, G.gs_step_params.n_visible.offset]
+                         G.gs_step_params.restate_ratio.offset, G.gs_step_params.n_visible.offset,
+                         G.gs_step_params.noise.offset, G.gs_step_params.aiu_scale.offset,
+                         G.gs_step_params.n_active.offset]
 
 
 def test_status_strings_and_version(G):
-    assert G.gs_abi_version() == 1
+    assert G.gs_abi_version() == 2
     assert G.status_name(G.GS_OK) == "GS_OK"
     assert G.status_name(G.GS_ERR_INVALID_ARG) == "GS_ERR_INVALID_ARG"
     assert G.status_name(99) == "GS_ERR_UNKNOWN"
