@@ -162,25 +162,29 @@ class Scene:
         self.CAMS = [G.make_camera(c) for c in self.cams]
         self.P = [self.params(k) for k in range(1, total_steps + 1)]
 
-    def params(self, k):
+    def params(self, k, **extra):
         wl = self.wl
         rs = k % wl.restate_every == 0
         return self.G.make_params(self.synth.lr_for_step(k, self.total), k, dar_opacity=wl.dar, dar_scale=wl.dar,
-                                  restate=rs, restate_ratio=wl.restate_ratio, seed=self.seed)
+                                  restate=rs, restate_ratio=wl.restate_ratio, seed=self.seed, **extra)
 
     def reset(self):
         for k, v in self.attrs.items():
             v.copy_(self.attrs0[k])
 
 
-def timed_run(G, sc, prec, steps, warmup, clocks_device=None, dist=None):
+def timed_run(G, sc, prec, steps, warmup, clocks_device=None, dist=None, extra=None):
     """Warm-up then `steps` timed launches of gs_step_camera on a fresh context;
-    CUDA events around the whole region and around every launch."""
+    CUDA events around the whole region and around every launch.  `extra`:
+    make_params keywords added to every step (the optional terms)."""
     import torch
     L = G.lib()
     sc.reset()
     h = G.gs_opt_init(G.make_config(n_pixels=sc.wl.n_pixels, prec=PREC_ENUM[prec]), sc.wl.n)
     counts = torch.zeros(warmup + steps, dtype=torch.int64, device="cuda")
+    P = sc.P
+    if extra:
+        P = [sc.params(k, **extra) for k in range(1, warmup + steps + 1)]
     stream = torch.cuda.current_stream()
     sh = ctypes.c_void_p(stream.cuda_stream)
     cnt = counts.data_ptr()
@@ -188,7 +192,7 @@ def timed_run(G, sc, prec, steps, warmup, clocks_device=None, dist=None):
     def launch(i):
         s = L.gs_step_camera(h, ctypes.byref(sc.A), ctypes.byref(sc.GB[i % len(sc.GB)]),
                              ctypes.byref(sc.CAMS[sc.order[i]]), None, ctypes.c_void_p(cnt + 8 * i),
-                             ctypes.byref(sc.P[i]), sh)
+                             ctypes.byref(P[i]), sh)
         if s != 0:
             raise G.GsError(s, "gs_step_camera")
 
@@ -343,6 +347,8 @@ def run_ours(args):
         out["mixed_precision"] = {"workload": f"{mwl.name}: {mwl.n} Gaussians, ~20% visible, {args.mixed_steps} "
                                               f"timed steps per format", "gate": "group relative L2 vs the FP32 step <= 1e-3",
                                   **legs}
+    if rank == 0 and args.next_rows:
+        out["next_rows"] = next_rows_leg(G, synth, args.next_steps)
     if rank == 0 and args.reindex:
         out["reindex"] = reindex_leg(G, synth, args.reindex_steps)
     if rank == 0 and args.batched:
@@ -353,6 +359,65 @@ def run_ours(args):
         print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def next_rows_leg(G, synth, steps, warmup=10, aiu_prob=0.1):
+    """The optional terms on the 1 M workload (FP32 moments), each timed as a
+    whole run like the headline: the active count alone, position noise on
+    the visible or on every primitive (App. Eq. disentangled_mu; eta_Ro 5e5,
+    lambda_mu 100, lambda_t 0.005 as in 3DGS-MCMC), AIU with probability
+    0.1 (Sec. 3.2), and gs_active_rows over 6 M logits.  Extra algorithmic
+    bytes over the plain step: 4 B per invisible row for the count (its
+    opacity), 44 B per invisible row for noise on every row (rotation,
+    scale, opacity read, xyz written), and per AIU row its attributes read
+    and written plus m, v and t read (948 B), counted at the expected number
+    of AIU rows aiu_prob * (N - N_v)."""
+    import torch
+    wl = synth.WORKLOADS[WORKLOAD]
+    sc = Scene(G, synth, wl, wl.seed, warmup + steps)
+    na = torch.zeros(1, dtype=torch.int64, device="cuda")
+    base = timed_run(G, sc, "fp32", steps, warmup)
+    variants = {
+        "active_count": (dict(n_active=na), 4, 0.0),
+        "noise_visible": (dict(noise=1, n_active=na), 4, 0.0),
+        "noise_all": (dict(noise=2, n_active=na), 4 + 44, 0.0),
+        "aiu_p0.1": (dict(aiu=True, aiu_prob=aiu_prob, aiu_scale=1.0), 0, aiu_prob * 948),
+    }
+    out = {"workload": f"{wl.name}: {wl.n} Gaussians, fp32 moments, {steps} timed steps per variant",
+           "plain": {"value": base["nv"] / base["elapsed"], "ms_per_step": base["elapsed"] / steps * 1e3,
+                     "hbm_gbs": base["bytes_per_launch"] / base["kern"] / 1e9}}
+    for name, (extra, b_inv, b_aiu) in variants.items():
+        r = timed_run(G, sc, "fp32", steps, warmup, extra=extra)
+        inv = wl.n - r["nv"] / steps
+        byt = r["bytes_per_launch"] + inv * (b_inv + b_aiu)
+        out[name] = {"value": r["nv"] / r["elapsed"], "ms_per_step": r["elapsed"] / steps * 1e3,
+                     "hbm_gbs": byt / r["kern"] / 1e9, "slowdown_vs_plain": r["kern"] / base["kern"]}
+    del sc
+    torch.cuda.empty_cache()
+    # prune list over 6 M logits
+    n = 6_000_000
+    gen = torch.Generator(device="cuda").manual_seed(1005)
+    tau = torch.randn(n, generator=gen, device="cuda") * 2.0 - 4.0
+    rows = torch.empty(n, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    h = G.gs_opt_init(G.make_config(), n)
+    for _ in range(3):
+        G.gs_active_rows(h, tau, rows, cnt)
+    torch.cuda.synchronize()
+    reps = 50
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        G.gs_active_rows(h, tau, rows, cnt)
+    e1.record()
+    torch.cuda.synchronize()
+    dt = e0.elapsed_time(e1) / 1e3 / reps
+    na_rows = int(cnt.item())
+    G.gs_opt_destroy(h)
+    out["active_rows_6m"] = {"ms": dt * 1e3, "n_active": na_rows,
+                             "hbm_gbs": (4 * n + 4 * na_rows) / dt / 1e9,
+                             "bytes": "4 B read per logit + 4 B written per active row (algorithmic)"}
+    return out
 
 
 HYB_STATE = 2 * (14 * 4 + 45 * 2) + 4     # m, v and t of one row in the hybrid format (B)
@@ -588,6 +653,8 @@ def main():
     ap.add_argument("--no-mixed-error", dest="mixed_error", action="store_false")
     ap.add_argument("--no-batched", dest="batched", action="store_false")
     ap.add_argument("--no-reindex", dest="reindex", action="store_false")
+    ap.add_argument("--no-next-rows", dest="next_rows", action="store_false")
+    ap.add_argument("--next-steps", type=int, default=300)
     ap.add_argument("--reindex-steps", type=int, default=1000)
     ap.add_argument("--batched-steps", type=int, default=100)
     ap.add_argument("--traffic", type=float, default=None,

@@ -4,16 +4,15 @@
 // Launched only when a step asks for one of them; the plain step kernel is
 // untouched by them.
 //
-// Per tile of 256 rows (one CTA of 256 threads):
-//   A. visibility, StSS, AIU and noise decisions per row; three
-//      shared-memory lists: visible rows, invisible rows with RSR and/or AIU,
-//      invisible rows with the noise only.  Rows no item will touch are
-//      counted for N_a here (their opacity is unchanged).
-//   B. items: the SH items of visible rows (as in the plain step), one row
-//      item per visible row for its 11 small columns; SH items and a row item
-//      per RSR/AIU row; a noise item per noise-only row.  A row item reads the
-//      rotation, scale and opacity before it updates any of them, so the noise
-//      of that row sees its values before this step.
+// Per tile of 256 rows (one CTA of 256 threads, 4 CTAs per SM as the plain
+// step):
+//   A. visibility, StSS, AIU and noise decisions per row.  A row that takes
+//      the noise has it computed here, from its values before this step, and
+//      kept in shared memory; a noise-only invisible row is finished here.
+//      Rows no item touches are counted for N_a here.  Two lists: visible
+//      rows, and invisible rows with RSR and/or AIU.
+//   B. the plain step's items: SH items and 3 small items per listed row.
+//      The xyz item subtracts the kept noise; the opacity item counts N_a.
 
 #include "step_common.cuh"
 
@@ -105,87 +104,98 @@ __device__ __forceinline__ void inv_sh_item(const StepArgs &a, const int32_t row
     }
 }
 
-// The 11 small columns (rotation, xyz, scale, opacity) of one row in one
-// item.  vis: Sparse Adam + DAR with this step's gradient and t += 1;
+// Small item c of a listed row, as small_item of the plain step, with the
+// optional terms.  vis: Sparse Adam + DAR, t += 1 (where chunk 14 keeps t);
 // otherwise kFAiu: the AIU step from the current moments.  kFRsr scales the
-// moments afterwards, kFNoise subtracts the position noise of the values
-// read at entry.  Returns whether the row is active after the step.
+// moments afterwards; chunk 13 subtracts the row's noise `nz` from xyz.
+// Chunk 14 returns whether the row is active after the step.
 template <int kPrec>
-__device__ __forceinline__ bool row_item(const StepArgs &a, const int32_t row, const bool vis, const uint8_t fl,
-                                         const float2 f)
+__device__ __forceinline__ bool small_item_x(const StepArgs &a, const int32_t row, const int c, const bool vis,
+                                             const uint8_t fl, const float2 f, const float3 nz)
 {
     using S = State<kPrec>;
-    const size_t r = (size_t)row;
-    float *px = a.a_xyz + r * 3, *ps = a.a_scale + r * 3, *pq = a.a_rot + r * 4, *po = a.a_op + r;
-    float4 q = ld4(pq);
-    float x0 = px[0], x1 = px[1], x2 = px[2];
-    float k0 = ps[0], k1 = ps[1], k2 = ps[2];
-    float tau = *po;
-    const float3 nz = (fl & kFNoise) ? noise_term(a, row, q, k0, k1, k2, tau) : make_float3(0.f, 0.f, 0.f);
     const bool aiu = !vis && (fl & kFAiu);
-    if (vis || aiu || (fl & kFRsr)) {
-        Chunk c12 = S::load_small(a, row, 12), c13 = S::load_small(a, row, 13), c14 = S::load_small(a, row, 14);
+    Chunk k = S::load_small(a, row, c);
+    float4 &m = k.m, &v = k.v;
+    const size_t r = (size_t)row;
+    bool active = false;
+    if (c == 12) {
+        float *pt = a.a_rot + r * 4;
+        if (vis || aiu) {
+            float4 th = ld4(pt);
+            const float l = a.lr[2];
+            if (vis) {
+                const float4 g = ldg4_stream(a.g_rot + r * 4);
+                th.x = step_element(th.x, g.x, m.x, v.x, f.x, f.y, a, l, false, 0.f, 0.f, 0.f);
+                th.y = step_element(th.y, g.y, m.y, v.y, f.x, f.y, a, l, false, 0.f, 0.f, 0.f);
+                th.z = step_element(th.z, g.z, m.z, v.z, f.x, f.y, a, l, false, 0.f, 0.f, 0.f);
+                th.w = step_element(th.w, g.w, m.w, v.w, f.x, f.y, a, l, false, 0.f, 0.f, 0.f);
+            } else {
+                const float la = l * a.aiu_scale;
+                th.x = aiu_element(th.x, m.x, v.x, f, a.eps, la);
+                th.y = aiu_element(th.y, m.y, v.y, f, a.eps, la);
+                th.z = aiu_element(th.z, m.z, v.z, f, a.eps, la);
+                th.w = aiu_element(th.w, m.w, v.w, f, a.eps, la);
+            }
+            st4(pt, th);
+        }
+    } else if (c == 13) {
+        float *px = a.a_xyz + r * 3;
+        float *ps = a.a_scale + r * 3;
+        float x0 = px[0], x1 = px[1], x2 = px[2], s0 = ps[0];
         if (vis) {
-            const float4 gq = ldg4_stream(a.g_rot + r * 4);
-            const float *gx = a.g_xyz + r * 3, *gs = a.g_scale + r * 3;
-            const float g0 = __ldcs(gx), g1 = __ldcs(gx + 1), g2 = __ldcs(gx + 2);
-            const float gs0 = __ldcs(gs), gs1 = __ldcs(gs + 1), gs2 = __ldcs(gs + 2), go = __ldcs(a.g_op + r);
-            const bool ds = a.dar_s != 0, dop = a.dar_o != 0;
-            // regulariser derivatives at the old values (App. Eqs. scale, opacity)
-            const float rs0 = ds ? expf(k0) : 0.f, rs1 = ds ? expf(k1) : 0.f, rs2 = ds ? expf(k2) : 0.f;
-            const float rop = dop ? dsigmoid(tau) : 0.f;
-            q.x = step_element(q.x, gq.x, c12.m.x, c12.v.x, f.x, f.y, a, a.lr[2], false, 0.f, 0.f, 0.f);
-            q.y = step_element(q.y, gq.y, c12.m.y, c12.v.y, f.x, f.y, a, a.lr[2], false, 0.f, 0.f, 0.f);
-            q.z = step_element(q.z, gq.z, c12.m.z, c12.v.z, f.x, f.y, a, a.lr[2], false, 0.f, 0.f, 0.f);
-            q.w = step_element(q.w, gq.w, c12.m.w, c12.v.w, f.x, f.y, a, a.lr[2], false, 0.f, 0.f, 0.f);
-            x0 = step_element(x0, g0, c13.m.x, c13.v.x, f.x, f.y, a, a.lr[0], false, 0.f, 0.f, 0.f);
-            x1 = step_element(x1, g1, c13.m.y, c13.v.y, f.x, f.y, a, a.lr[0], false, 0.f, 0.f, 0.f);
-            x2 = step_element(x2, g2, c13.m.z, c13.v.z, f.x, f.y, a, a.lr[0], false, 0.f, 0.f, 0.f);
-            k0 = step_element(k0, gs0, c13.m.w, c13.v.w, f.x, f.y, a, a.lr[1], ds, rs0, a.lam_s, a.clip_s);
-            k1 = step_element(k1, gs1, c14.m.x, c14.v.x, f.x, f.y, a, a.lr[1], ds, rs1, a.lam_s, a.clip_s);
-            k2 = step_element(k2, gs2, c14.m.y, c14.v.y, f.x, f.y, a, a.lr[1], ds, rs2, a.lam_s, a.clip_s);
-            tau = step_element(tau, go, c14.m.z, c14.v.z, f.x, f.y, a, a.lr[3], dop, rop, a.lam_o, a.clip_o);
-            if (!S::kTInSh) c14.t += 1u;       // the row's own step count (Sec. 3.2)
+            const float *gx = a.g_xyz + r * 3;
+            const float g0 = __ldcs(gx), g1 = __ldcs(gx + 1), g2 = __ldcs(gx + 2), gs0 = __ldcs(a.g_scale + r * 3);
+            const bool ds = a.dar_s != 0;
+            const float r0s = ds ? expf(s0) : 0.f;
+            x0 = step_element(x0, g0, m.x, v.x, f.x, f.y, a, a.lr[0], false, 0.f, 0.f, 0.f);
+            x1 = step_element(x1, g1, m.y, v.y, f.x, f.y, a, a.lr[0], false, 0.f, 0.f, 0.f);
+            x2 = step_element(x2, g2, m.z, v.z, f.x, f.y, a, a.lr[0], false, 0.f, 0.f, 0.f);
+            s0 = step_element(s0, gs0, m.w, v.w, f.x, f.y, a, a.lr[1], ds, r0s, a.lam_s, a.clip_s);
         } else if (aiu) {
-            const float lq = a.lr[2] * a.aiu_scale, lx = a.lr[0] * a.aiu_scale, ls = a.lr[1] * a.aiu_scale,
-                        lo = a.lr[3] * a.aiu_scale;
-            q.x = aiu_element(q.x, c12.m.x, c12.v.x, f, a.eps, lq);
-            q.y = aiu_element(q.y, c12.m.y, c12.v.y, f, a.eps, lq);
-            q.z = aiu_element(q.z, c12.m.z, c12.v.z, f, a.eps, lq);
-            q.w = aiu_element(q.w, c12.m.w, c12.v.w, f, a.eps, lq);
-            x0 = aiu_element(x0, c13.m.x, c13.v.x, f, a.eps, lx);
-            x1 = aiu_element(x1, c13.m.y, c13.v.y, f, a.eps, lx);
-            x2 = aiu_element(x2, c13.m.z, c13.v.z, f, a.eps, lx);
-            k0 = aiu_element(k0, c13.m.w, c13.v.w, f, a.eps, ls);
-            k1 = aiu_element(k1, c14.m.x, c14.v.x, f, a.eps, ls);
-            k2 = aiu_element(k2, c14.m.y, c14.v.y, f, a.eps, ls);
-            tau = aiu_element(tau, c14.m.z, c14.v.z, f, a.eps, lo);
+            const float lx = a.lr[0] * a.aiu_scale;
+            x0 = aiu_element(x0, m.x, v.x, f, a.eps, lx);
+            x1 = aiu_element(x1, m.y, v.y, f, a.eps, lx);
+            x2 = aiu_element(x2, m.z, v.z, f, a.eps, lx);
+            s0 = aiu_element(s0, m.w, v.w, f, a.eps, a.lr[1] * a.aiu_scale);
         }
-        if (fl & kFRsr) {      // RSR post-scale (Eq. meth::restate); chunk 14 holds 3 moments
-            c12.m.x *= a.alpha1; c12.m.y *= a.alpha1; c12.m.z *= a.alpha1; c12.m.w *= a.alpha1;
-            c12.v.x *= a.alpha2; c12.v.y *= a.alpha2; c12.v.z *= a.alpha2; c12.v.w *= a.alpha2;
-            c13.m.x *= a.alpha1; c13.m.y *= a.alpha1; c13.m.z *= a.alpha1; c13.m.w *= a.alpha1;
-            c13.v.x *= a.alpha2; c13.v.y *= a.alpha2; c13.v.z *= a.alpha2; c13.v.w *= a.alpha2;
-            c14.m.x *= a.alpha1; c14.m.y *= a.alpha1; c14.m.z *= a.alpha1;
-            c14.v.x *= a.alpha2; c14.v.y *= a.alpha2; c14.v.z *= a.alpha2;
+        if (vis || aiu || (fl & kFNoise)) {
+            __stcs(px, x0 - nz.x); __stcs(px + 1, x1 - nz.y); __stcs(px + 2, x2 - nz.z);
         }
-        if (vis || (fl & kFRsr)) {             // an AIU step leaves the moments as they are
-            S::store_small(a, row, 12, c12);
-            S::store_small(a, row, 13, c13);
-            S::store_small(a, row, 14, c14);
+        if (vis || aiu) __stcs(ps, s0);
+    } else {
+        float *ps = a.a_scale + r * 3;
+        float *po = a.a_op + r;
+        float s1 = ps[1], s2 = ps[2], op = *po;
+        if (vis) {
+            const float *gsp = a.g_scale + r * 3;
+            const float gs1 = __ldcs(gsp + 1), gs2 = __ldcs(gsp + 2), go = __ldcs(a.g_op + r);
+            const bool ds = a.dar_s != 0, dop = a.dar_o != 0;
+            const float r1s = ds ? expf(s1) : 0.f, r2s = ds ? expf(s2) : 0.f;
+            const float rop = dop ? dsigmoid(op) : 0.f;
+            s1 = step_element(s1, gs1, m.x, v.x, f.x, f.y, a, a.lr[1], ds, r1s, a.lam_s, a.clip_s);
+            s2 = step_element(s2, gs2, m.y, v.y, f.x, f.y, a, a.lr[1], ds, r2s, a.lam_s, a.clip_s);
+            op = step_element(op, go, m.z, v.z, f.x, f.y, a, a.lr[3], dop, rop, a.lam_o, a.clip_o);
+            if (!S::kTInSh) k.t += 1u;         // the row's own step count (Sec. 3.2)
+        } else if (aiu) {
+            const float ls = a.lr[1] * a.aiu_scale;
+            s1 = aiu_element(s1, m.x, v.x, f, a.eps, ls);
+            s2 = aiu_element(s2, m.y, v.y, f, a.eps, ls);
+            op = aiu_element(op, m.z, v.z, f, a.eps, a.lr[3] * a.aiu_scale);
         }
         if (vis || aiu) {
-            st4(pq, q);
-            __stcs(ps, k0); __stcs(ps + 1, k1); __stcs(ps + 2, k2);
-            __stcs(po, tau);
+            __stcs(ps + 1, s1); __stcs(ps + 2, s2);
+            __stcs(po, op);
         }
+        active = op > a.tau_act;
     }
-    if (vis || aiu || (fl & kFNoise)) {
-        __stcs(px, x0 - nz.x);
-        __stcs(px + 1, x1 - nz.y);
-        __stcs(px + 2, x2 - nz.z);
+    if (fl & kFRsr) {      // RSR post-scale (Eq. meth::restate); chunk 14 holds 3 moments
+        m.x *= a.alpha1; m.y *= a.alpha1; m.z *= a.alpha1;
+        v.x *= a.alpha2; v.y *= a.alpha2; v.z *= a.alpha2;
+        if (c != 14) { m.w *= a.alpha1; v.w *= a.alpha2; }
     }
-    return tau > a.tau_act;
+    if (vis || (fl & kFRsr)) S::store_small(a, row, c, k);    // an AIU step keeps the moments
+    return active;
 }
 
 // Shared-memory lists of one tile of the extended step.
@@ -193,12 +203,13 @@ template <int kTile>
 struct TileListsX {
     int32_t list[kTile];      // visible rows
     int32_t ilist[kTile];     // invisible rows with RSR and/or AIU
-    int32_t nlist[kTile];     // invisible rows with the noise only
     float2 fac[kTile];        // bias factors of the visible rows (count t + 1)
     float2 ifac[kTile];       // bias factors of the AIU rows (count t)
+    float3 nz[kTile];         // noise of the visible rows (zero without)
+    float3 inz[kTile];        // noise of the listed invisible rows
     uint8_t vflag[kTile];
     uint8_t iflag[kTile];
-    int32_t cnt[3][kTile / 32];
+    int32_t cnt[2][kTile / 32];
     unsigned active;
 };
 
@@ -207,36 +218,34 @@ __device__ __forceinline__ float2 factors(const StepArgs &a, uint32_t k)
     return k < (uint32_t)a.fac_len ? a.fac[k] : make_float2(1.0f, 1.0f);
 }
 
-// Phase A of the extended step; returns the three list lengths.
+// Phase A of the extended step; returns the two list lengths.
 template <int kTile, int kRowBytes, int kTByte>
 __device__ __forceinline__ void tile_decide_x(const StepArgs &a, const int vis_src, const int64_t r0,
-                                              TileListsX<kTile> &L, int &nv, int &ni, int &nn)
+                                              TileListsX<kTile> &L, int &nv, int &ni)
 {
     constexpr int kRpt = kTile / kThreads;
     constexpr int kWarps = kThreads / 32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nrow = (int)min((int64_t)kTile, (int64_t)a.n_rows - r0);
-    unsigned bal_v[kRpt], bal_i[kRpt], bal_n[kRpt];
+    unsigned bal_v[kRpt], bal_i[kRpt];
     uint8_t flag[kRpt];
     uint32_t t_old[kRpt];
+    float3 nz[kRpt];
     unsigned my_active = 0;
 #pragma unroll
     for (int j = 0; j < kRpt; ++j) {
         const int lr = j * kThreads + tid;
         const int64_t row = r0 + lr;
         const bool in = lr < nrow;
-        bool vis = false, in_i = false, in_n = false;
+        bool vis = false, in_i = false;
         uint8_t fl = 0;
         t_old[j] = 0;
+        nz[j] = make_float3(0.f, 0.f, 0.f);
         if (in) {
-            if (vis_src == kVisCamera) {
-                const float *p = a.a_xyz + row * 3;
-                vis = frustum_visible(p[0], p[1], p[2], a.cam);
-            } else if (vis_src == kVisMask) {
-                vis = a.mask_in[row] != 0;
-            } else {
-                vis = true;
-            }
+            const float *p = a.a_xyz + row * 3;
+            if (vis_src == kVisCamera) vis = frustum_visible(p[0], p[1], p[2], a.cam);
+            else if (vis_src == kVisMask) vis = a.mask_in[row] != 0;
+            else vis = true;
             if (a.mask_out) a.mask_out[row] = vis ? 1 : 0;
             if (a.restate && stss_sampled(a, (int32_t)row)) fl |= kFRsr;
             if (a.noise == GS_NOISE_ALL || (a.noise == GS_NOISE_VISIBLE && vis)) fl |= kFNoise;
@@ -247,17 +256,26 @@ __device__ __forceinline__ void tile_decide_x(const StepArgs &a, const int vis_s
             // a primitive never seen has no moments: its AIU step is zero
             if (aiu_draw && (a.bias_mode || t_old[j] > 0u)) fl |= kFAiu;
             in_i = !vis && (fl & (kFRsr | kFAiu));
-            in_n = !vis && !in_i && (fl & kFNoise);
-            if (a.n_active && !vis && !in_i) my_active += a.a_op[row] > a.tau_act ? 1u : 0u;
+            float tau = 0.f;
+            if ((fl & kFNoise) || (a.n_active && !vis && !in_i)) tau = a.a_op[row];
+            if (fl & kFNoise) {
+                const float4 q = ld4(a.a_rot + row * 4);
+                const float *ps = a.a_scale + row * 3;
+                nz[j] = noise_term(a, (int32_t)row, q, ps[0], ps[1], ps[2], tau);
+                if (!vis && !in_i) {           // noise-only row: finished here
+                    float *px = a.a_xyz + row * 3;
+                    const float x0 = px[0], x1 = px[1], x2 = px[2];
+                    __stcs(px, x0 - nz[j].x); __stcs(px + 1, x1 - nz[j].y); __stcs(px + 2, x2 - nz[j].z);
+                }
+            }
+            if (a.n_active && !vis && !in_i) my_active += tau > a.tau_act ? 1u : 0u;
         }
         flag[j] = fl;
         bal_v[j] = __ballot_sync(0xffffffffu, vis);
         bal_i[j] = __ballot_sync(0xffffffffu, in_i);
-        bal_n[j] = __ballot_sync(0xffffffffu, in_n);
         if (lane == 0) {
             L.cnt[0][j * kWarps + warp] = __popc(bal_v[j]);
             L.cnt[1][j * kWarps + warp] = __popc(bal_i[j]);
-            L.cnt[2][j * kWarps + warp] = __popc(bal_n[j]);
         }
     }
     if (tid == 0) L.active = 0u;
@@ -266,21 +284,19 @@ __device__ __forceinline__ void tile_decide_x(const StepArgs &a, const int vis_s
         my_active = __reduce_add_sync(0xffffffffu, my_active);
         if (lane == 0 && my_active) atomicAdd(&L.active, my_active);
     }
-    nv = ni = nn = 0;
+    nv = ni = 0;
     for (int q = 0; q < kRpt * kWarps; ++q) {
         nv += L.cnt[0][q];
         ni += L.cnt[1][q];
-        nn += L.cnt[2][q];
     }
     const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
     for (int j = 0; j < kRpt; ++j) {
         const int me = j * kWarps + warp;
-        int bv = 0, bi = 0, bn = 0;
+        int bv = 0, bi = 0;
         for (int q = 0; q < me; ++q) {
             bv += L.cnt[0][q];
             bi += L.cnt[1][q];
-            bn += L.cnt[2][q];
         }
         const int32_t row = (int32_t)(r0 + j * kThreads + tid);
         const unsigned me_bit = 1u << lane;
@@ -289,6 +305,7 @@ __device__ __forceinline__ void tile_decide_x(const StepArgs &a, const int vis_s
             L.list[pos] = row;
             L.vflag[pos] = flag[j];
             L.fac[pos] = factors(a, a.bias_mode ? a.k_bias : t_old[j] + 1u);
+            L.nz[pos] = nz[j];
         }
         if (bal_i[j] & me_bit) {
             const int pos = bi + __popc(bal_i[j] & lt);
@@ -296,8 +313,8 @@ __device__ __forceinline__ void tile_decide_x(const StepArgs &a, const int vis_s
             L.iflag[pos] = flag[j];
             L.ifac[pos] = (flag[j] & kFAiu) ? factors(a, a.bias_mode ? a.k_bias : t_old[j])
                                             : make_float2(1.0f, 1.0f);
+            L.inz[pos] = nz[j];
         }
-        if (bal_n[j] & me_bit) L.nlist[bn + __popc(bal_n[j] & lt)] = row;
     }
     if (tid == 0 && a.n_visible && nv) atomicAdd(a.n_visible, (unsigned long long)nv);
     __syncthreads();
@@ -311,28 +328,29 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) step_tile_x(const StepAr
     constexpr int kNsh = 48 / kW;
     __shared__ TileListsX<kTile> L;
     const int64_t r0 = (int64_t)blockIdx.x * kTile;
-    int nv, ni, nn;
-    tile_decide_x<kTile, S::kRowBytes, S::kTByte>(a, vis_src, r0, L, nv, ni, nn);
+    int nv, ni;
+    tile_decide_x<kTile, S::kRowBytes, S::kTByte>(a, vis_src, r0, L, nv, ni);
 
     unsigned my_active = 0;
-    const int e_sh = kNsh * nv, e_vis = e_sh + nv, e_ish = e_vis + kNsh * ni, e_inv = e_ish + ni, e_all = e_inv + nn;
+    const int e_sh = kNsh * nv, e_vis = e_sh + 3 * nv, e_ish = e_vis + kNsh * ni, e_all = e_ish + 3 * ni;
     for (int w = threadIdx.x; w < e_all; w += kThreads) {
         if (w < e_sh) {
             const int j = w / kNsh, i = w - j * kNsh;
             sh_item<kPrec, kW>(a, L.list[j], i, (L.vflag[j] & kFRsr) != 0, L.fac[j]);
         } else if (w < e_vis) {
-            const int j = w - e_sh;
-            my_active += row_item<kPrec>(a, L.list[j], true, L.vflag[j], L.fac[j]) ? 1u : 0u;
+            const int q = w - e_sh;
+            const int j = q % nv, c = 12 + q / nv;
+            const bool act = small_item_x<kPrec>(a, L.list[j], c, true, L.vflag[j], L.fac[j], L.nz[j]);
+            my_active += (c == 14 && act) ? 1u : 0u;
         } else if (w < e_ish) {
             const int q = w - e_vis;
             const int j = q / kNsh, i = q - j * kNsh;
             inv_sh_item<kPrec, kW>(a, L.ilist[j], i, L.iflag[j], L.ifac[j]);
-        } else if (w < e_inv) {
-            const int j = w - e_ish;
-            my_active += row_item<kPrec>(a, L.ilist[j], false, L.iflag[j], L.ifac[j]) ? 1u : 0u;
         } else {
-            const int32_t row = L.nlist[w - e_inv];
-            row_item<kPrec>(a, row, false, kFNoise, make_float2(1.0f, 1.0f));
+            const int q = w - e_ish;
+            const int j = q % ni, c = 12 + q / ni;
+            const bool act = small_item_x<kPrec>(a, L.ilist[j], c, false, L.iflag[j], L.ifac[j], L.inz[j]);
+            my_active += (c == 14 && act) ? 1u : 0u;
         }
     }
     if (a.n_active) {
@@ -346,7 +364,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) step_tile_x(const StepAr
 }  // namespace
 
 constexpr int kExtTile = 256;
-constexpr int kExtMinBlocks = 2;
+constexpr int kExtMinBlocks = 4;
 
 cudaError_t launch_step_ext(const StepArgs &a, int prec, int vis_src, cudaStream_t s)
 {
