@@ -278,6 +278,28 @@ struct State<GS_MOM_BF16_HYBRID> {
     }
 };
 
+// Ask L2 to fetch the contiguous parts a visible row's items will read (SH
+// attributes and gradients, m and v rows; cp.async.bulk.prefetch.L2), as
+// soon as the row is known to be visible.  Worth it for sparse tiles: their
+// rows are scattered, and the items' later loads then hit L2.  Dense tiles
+// already stream well and only pay for the extra requests, so callers skip
+// the hint when most of the tile is visible.
+template <int kRowBytes>
+__device__ __forceinline__ void prefetch_row_l2(const StepArgs &a, int32_t row)
+{
+    const size_t r = (size_t)row;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], 192;" ::"l"(a.a_sh + r * 48) : "memory");
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], 192;" ::"l"(a.g_sh + r * 48) : "memory");
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(static_cast<const char *>(a.m) + r * kRowBytes),
+                 "n"(kRowBytes) : "memory");
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(static_cast<const char *>(a.v) + r * kRowBytes),
+                 "n"(kRowBytes) : "memory");
+}
+
+// Prefetch when at most 60 % of the tile's rows are visible.
+template <int kTile>
+__device__ __forceinline__ bool sparse_tile(int nv) { return 5 * nv <= 3 * kTile; }
+
 // ---------------------------------------------------------------- the items
 
 // SH item i of a visible row: SH columns kW*i .. kW*i+kW-1 (0-2 are the DC

@@ -303,6 +303,7 @@ __device__ __forceinline__ void tile_decide_x(const StepArgs &a, const int vis_s
         if (bal_v[j] & me_bit) {
             const int pos = bv + __popc(bal_v[j] & lt);
             L.list[pos] = row;
+            if (sparse_tile<kTile>(nv)) prefetch_row_l2<kRowBytes>(a, row);
             L.vflag[pos] = flag[j];
             L.fac[pos] = factors(a, a.bias_mode ? a.k_bias : t_old[j] + 1u);
             L.nz[pos] = nz[j];

@@ -38,8 +38,9 @@ struct TileLists {
 
 // Decide visibility and StSS membership for the tile's rows, prefetch the
 // step counters of visible rows (at byte kTByte of their m row), and compact
-// both row sets into `L`.  Returns the visible count in nv and the
-// invisible-sampled count in nr.
+// both row sets into `L`; in a sparse tile, ask L2 for each visible row's
+// data.  Returns the visible count in nv and the invisible-sampled count in
+// nr.
 template <int kTile, int kRowBytes, int kTByte>
 __device__ __forceinline__ void tile_decide(const StepArgs &a, const int vis_src, const int64_t r0, TileLists<kTile> &L,
                                             int &nv, int &nr)
@@ -102,6 +103,7 @@ __device__ __forceinline__ void tile_decide(const StepArgs &a, const int vis_src
             const bool smp = (bal_s[j] >> lane) & 1u;
             const int pos = bv + __popc(bal_v[j] & lt);
             L.list[pos] = row | (smp ? (int32_t)0x80000000 : 0);
+            if (sparse_tile<kTile>(nv)) prefetch_row_l2<kRowBytes>(a, row);
             const uint32_t tb = a.bias_mode ? a.k_bias : t_old[j] + 1u;
             L.fac[pos] = (tb < (uint32_t)a.fac_len) ? a.fac[tb] : make_float2(1.0f, 1.0f);
         }
