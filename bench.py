@@ -43,8 +43,10 @@ MIXED_WORKLOAD = "c3_3m"
 # values each), m and v read + write in the storage format, t read + write;
 # minus the row's 12-B mean, whose read is already counted by the frustum test.
 # FP32 moments 4 * 236 B; hybrid 4 * (45 * 2 + 14 * 4) B; BF16 4 * 59 * 2 B.
-STATE_RW = {"fp32": 4 * 236, "bf16_hybrid": 4 * (45 * 2 + 14 * 4), "bf16": 4 * 118}
-PREC_ENUM = {"fp32": 0, "bf16": 1, "bf16_hybrid": 3}
+# FP16-block: 4 * (59 FP16 values + 8 group exponent bytes); its t is a uint16.
+STATE_RW = {"fp32": 4 * 236, "bf16_hybrid": 4 * (45 * 2 + 14 * 4), "bf16": 4 * 118, "fp16_block": 4 * (118 + 8)}
+T_RW = {"fp32": 8, "bf16_hybrid": 8, "bf16": 8, "fp16_block": 4}
+PREC_ENUM = {"fp32": 0, "bf16": 1, "bf16_hybrid": 3, "fp16_block": 4}
 BYTES_ROW_VIS = 12          # every row: the mean read by the frustum test
 # DRAM bytes (read + write) of one step_tile launch from an ncu capture of the
 # current kernel, with the algorithmic bytes of that same launch
@@ -54,7 +56,7 @@ NCU_TRAFFIC = {("c2_1m", "fp32"): (541.905152e6, 476.3e6),
 
 
 def bytes_visible(prec: str) -> int:
-    return 3 * 236 + STATE_RW[prec] + 8 - 12
+    return 3 * 236 + STATE_RW[prec] + T_RW[prec] - 12
 
 
 def _peaks():
@@ -335,14 +337,14 @@ def run_ours(args):
         mwl = synth.WORKLOADS[MIXED_WORKLOAD]
         msc = Scene(G, synth, mwl, mwl.seed, max(1000, args.mixed_steps + 10))
         legs = {}
-        for prec in ("fp32", "bf16_hybrid", "bf16"):
+        for prec in ("fp32", "fp16_block", "bf16_hybrid", "bf16"):
             rr = timed_run(G, msc, prec, args.mixed_steps, 10)
             legs[prec] = {"value": rr["nv"] / rr["elapsed"], "hbm_gbs": rr["bytes_per_launch"] / rr["kern"] / 1e9,
                           "ms_per_step": rr["elapsed"] / args.mixed_steps * 1e3,
                           "bytes_per_launch": rr["bytes_per_launch"]}
             if args.mixed_error and prec != "fp32":
                 legs[prec]["error"] = error_vs_fp32(G, msc, prec)
-        for prec in ("bf16_hybrid", "bf16"):
+        for prec in ("fp16_block", "bf16_hybrid", "bf16"):
             legs[prec]["speedup_vs_fp32"] = legs[prec]["value"] / legs["fp32"]["value"]
         out["mixed_precision"] = {"workload": f"{mwl.name}: {mwl.n} Gaussians, ~20% visible, {args.mixed_steps} "
                                               f"timed steps per format", "gate": "group relative L2 vs the FP32 step <= 1e-3",
@@ -417,6 +419,43 @@ def next_rows_leg(G, synth, steps, warmup=10, aiu_prob=0.1):
     out["active_rows_6m"] = {"ms": dt * 1e3, "n_active": na_rows,
                              "hbm_gbs": (4 * n + 4 * na_rows) / dt / 1e9,
                              "bytes": "4 B read per logit + 4 B written per active row (algorithmic)"}
+    return out
+
+
+def density_sweep(G, synth, densities=(1.0, 0.6, 0.3, 0.1, 0.05), steps=200, warmup=20):
+    """The plain FP32 step on the 1 M scene with caller masks of random rows
+    at each density: how the achieved bandwidth depends on how scattered the
+    visible rows are."""
+    import torch
+    wl = synth.WORKLOADS[WORKLOAD]
+    n = wl.n
+    groups = synth.scene_blobs(n, wl.seed, wl.extent)
+    attrs = {k: torch.from_numpy(v).cuda() for k, v in groups.items()}
+    gen = torch.Generator(device="cuda").manual_seed(1)
+    gb = [{nm: torch.randn((n, w), generator=gen, device="cuda") * 1e-3 for nm, w in synth.GROUPS} for _ in range(4)]
+    A, GB = G.make_attrs(attrs), [G.make_attrs(g) for g in gb]
+    h = G.gs_opt_init(G.make_config(n_pixels=wl.n_pixels), n)
+    rng = np.random.default_rng(0)
+    peak, _ = _peaks()
+    out = {"workload": f"{wl.name} scene, random-row masks, fp32 moments, {steps} steps per density"}
+    for dens in densities:
+        masks = [torch.from_numpy((rng.random(n) < dens).astype(np.uint8)).cuda() for _ in range(4)]
+        nvis = [int(m.sum().item()) for m in masks]
+        P = [G.make_params(synth.lr_for_step(k, 1000), k) for k in range(1, warmup + steps + 1)]
+        for i in range(warmup):
+            G.gs_step(h, A, GB[i % 4], masks[i % 4], P[i])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for i in range(warmup, warmup + steps):
+            G.gs_step(h, A, GB[i % 4], masks[i % 4], P[i])
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        nv = sum(nvis[i % 4] for i in range(warmup, warmup + steps)) / steps
+        gbs = (nv * (3 * 236 + STATE_RW["fp32"] + 8 - 12 + 12) + n) / ms / 1e6    # + xyz of visible rows, mask
+        out[str(dens)] = {"ms": ms, "hbm_gbs": gbs, "frac": gbs / peak}
+    G.gs_opt_destroy(h)
     return out
 
 
@@ -654,6 +693,8 @@ def main():
     ap.add_argument("--no-batched", dest="batched", action="store_false")
     ap.add_argument("--no-reindex", dest="reindex", action="store_false")
     ap.add_argument("--no-next-rows", dest="next_rows", action="store_false")
+    ap.add_argument("--density-sweep", action="store_true",
+                    help="only time the plain step at several visible densities (random-row masks)")
     ap.add_argument("--next-steps", type=int, default=300)
     ap.add_argument("--reindex-steps", type=int, default=1000)
     ap.add_argument("--batched-steps", type=int, default=100)
@@ -664,6 +705,12 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.density_sweep:
+        from paper_2601_16736_gb300 import build as B
+        B.build()
+        from paper_2601_16736_gb300 import gsopt as G
+        from paper_2601_16736_gb300 import synth
+        print(json.dumps({"density_sweep": density_sweep(G, synth)}))
     else:
         run_ours(args)
 

@@ -75,9 +75,20 @@ typedef enum gs_moment_prec {
     GS_MOM_FP32 = 0,
     GS_MOM_BF16 = 1,        /* all 59 columns BF16, round-to-nearest-even             */
     GS_MOM_FP8E4M3 = 2,     /* reserved: returns GS_ERR_UNSUPPORTED                    */
-    GS_MOM_BF16_HYBRID = 3  /* the 45 SH-rest columns BF16 (m round-to-nearest, v
+    GS_MOM_BF16_HYBRID = 3, /* the 45 SH-rest columns BF16 (m round-to-nearest, v
                                stochastically rounded from a counter hash of (seed,
                                iteration, row, slot)); the other 14 columns FP32  */
+    GS_MOM_FP16_BLOCK = 4   /* all 59 columns FP16 with one shared exponent per
+                               group of columns a work item updates (8 SH columns;
+                               rotation; xyz + scale + opacity): the group's largest
+                               magnitude is scaled into FP16's top binade, so every
+                               value within 2^29 of it keeps FP16's 10-bit mantissa.
+                               m rounded to nearest, v stochastically (13 bits from
+                               the same hash).  128 B per moment and row, as BF16.
+                               The step count t saturates at 65535 (the
+                               bias-correction factors are exactly 1 from step
+                               15936 on).  Not available with position noise, AIU,
+                               the active count or gs_batch_*.                    */
 } gs_moment_prec;
 
 /* Regulariser form.  GS_REG_DAR is the paper's AdamW-GS (Eq. disentangled_adam);

@@ -51,7 +51,10 @@ constexpr int32_t kMaxTable = 1 << 22;
 
 size_t state_row_bytes(int prec)
 {
-    return prec == GS_MOM_FP32 ? gs::kRowBytesF32 : prec == GS_MOM_BF16 ? gs::kRowBytesBf16 : gs::kRowBytesHyb;
+    return prec == GS_MOM_FP32 ? gs::kRowBytesF32
+           : prec == GS_MOM_BF16 ? gs::kRowBytesBf16
+           : prec == GS_MOM_FP16_BLOCK ? gs::kRowBytesF16B
+                                   : gs::kRowBytesHyb;
 }
 
 gs_status fail_cuda(gs_opt *o, cudaError_t e)
@@ -216,6 +219,13 @@ float active_threshold()
     return c;
 }
 
+// The optional terms (noise, AIU, active count) run in the extended step,
+// which has no FP16-block variant.
+bool ext_unsupported(const gs_opt *o, const gs_step_params *p)
+{
+    return o->cfg.prec == GS_MOM_FP16_BLOCK && (p->noise || p->aiu || p->n_active);
+}
+
 void fill_args(const gs_opt *o, const gs_step_params *p, StepArgs *a)
 {
     memset(a, 0, sizeof(*a));
@@ -304,7 +314,7 @@ gs_status gs_opt_init(gs_opt **out, const gs_opt_config *cfg, int64_t n_rows, vo
         !finite(c.clip_s))
         return GS_ERR_INVALID_ARG;
     if (!(c.alpha1 >= 0.0f && c.alpha1 < 1.0f && c.alpha2 >= 0.0f && c.alpha2 < 1.0f)) return GS_ERR_INVALID_ARG;
-    if (c.prec < GS_MOM_FP32 || c.prec > GS_MOM_BF16_HYBRID) return GS_ERR_INVALID_ARG;
+    if (c.prec < GS_MOM_FP32 || c.prec > GS_MOM_FP16_BLOCK) return GS_ERR_INVALID_ARG;
     if (c.bias_mode != 0 && c.bias_mode != 1) return GS_ERR_INVALID_ARG;
     if (c.reg_mode < GS_REG_DAR || c.reg_mode > GS_REG_ADAMW_CLIP || c.reserved != 0) return GS_ERR_INVALID_ARG;
     if (c.reg_mode == GS_REG_DAR && c.n_pixels <= 0) return GS_ERR_INVALID_ARG;
@@ -399,6 +409,7 @@ gs_status gs_step(gs_opt *o, const gs_attrs *attrs, const gs_grads *grads, const
     if (st != GS_OK) return st;
     const int64_t n = o->n_rows;
     if (!attrs || !grads || !params_ok(o, params)) return GS_ERR_INVALID_ARG;
+    if (ext_unsupported(o, params)) return GS_ERR_UNSUPPORTED;
     if (!attrs_ok(o, *attrs, n) || !attrs_ok(o, *grads, n) || !dev_ok(o, mask, mask ? (size_t)n : 0, 1))
         return GS_ERR_INVALID_ARG;
     StepArgs a;
@@ -416,6 +427,7 @@ gs_status gs_step_camera(gs_opt *o, const gs_attrs *attrs, const gs_grads *grads
     if (st != GS_OK) return st;
     const int64_t n = o->n_rows;
     if (!attrs || !grads || !camera_ok(cam) || !params_ok(o, params)) return GS_ERR_INVALID_ARG;
+    if (ext_unsupported(o, params)) return GS_ERR_UNSUPPORTED;
     if (!attrs_ok(o, *attrs, n) || !attrs_ok(o, *grads, n) || !dev_ok(o, mask_out, mask_out ? (size_t)n : 0, 1) ||
         !dev_ok(o, n_visible, n_visible ? 8 : 0, 8))
         return GS_ERR_INVALID_ARG;
@@ -436,6 +448,7 @@ gs_status gs_step_host(gs_opt *o, const gs_attrs *attrs, const gs_grads *gh, con
     if (st != GS_OK) return st;
     const int64_t n = o->n_rows;
     if (!attrs || !gh || !camera_ok(cam) || !params_ok(o, params) || !n_visible_host) return GS_ERR_INVALID_ARG;
+    if (ext_unsupported(o, params)) return GS_ERR_UNSUPPORTED;
     if (n && (!gh->xyz || !gh->scale || !gh->rot || !gh->opacity || !gh->sh)) return GS_ERR_INVALID_ARG;
     if (!attrs_ok(o, *attrs, n)) return GS_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -907,6 +920,7 @@ extern "C" gs_status gs_step_host_noalloc(gs_opt *o, const gs_attrs *attrs, cons
     const int64_t n = o->n_rows;
     if (n > (int64_t)kNaRows) return GS_ERR_INVALID_ARG;
     if (!attrs || !gh || !camera_ok(cam) || !params_ok(o, params) || !n_visible_host) return GS_ERR_INVALID_ARG;
+    if (ext_unsupported(o, params)) return GS_ERR_UNSUPPORTED;
     if (n && (!gh->xyz || !gh->scale || !gh->rot || !gh->opacity || !gh->sh)) return GS_ERR_INVALID_ARG;
     if (!attrs_ok(o, *attrs, n)) return GS_ERR_INVALID_ARG;
     float *base = noalloc_scratch(o->device);

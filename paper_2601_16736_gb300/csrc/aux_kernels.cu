@@ -181,6 +181,67 @@ __global__ void import_kernel(const StateView st, int32_t n, const float *__rest
     if (t_in && c == 0) *t_of(st, r) = t_in[r];
 }
 
+// FP16-block rows: export decodes one value per thread (its group exponent
+// beside it); import encodes one group per thread (8 SH columns, rotation,
+// xyz + scale + opacity) so that the group's shared exponent can be chosen,
+// rounding to nearest.  t is a uint16 at kTByteF16B (saturated on import).
+__global__ void export_f16b_kernel(const StateView st, int32_t n, float *__restrict__ m_out,
+                                   float *__restrict__ v_out, uint32_t *__restrict__ t_out)
+{
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (int64_t)n * kNumCols) return;
+    const int64_t r = gid / kNumCols;
+    const int c = (int)(gid - r * kNumCols);
+    int byte, group;
+    f16b_slot(c, byte, group);
+    const char *mr = static_cast<const char *>(st.m) + r * kRowBytesF16B;
+    const char *vr = static_cast<const char *>(st.v) + r * kRowBytesF16B;
+    if (m_out)
+        m_out[gid] = __half2float(*reinterpret_cast<const __half *>(mr + byte)) * dec_scale((uint8_t)mr[kF16BExp + group]);
+    if (v_out)
+        v_out[gid] = __half2float(*reinterpret_cast<const __half *>(vr + byte)) * dec_scale((uint8_t)vr[kF16BExp + group]);
+    if (t_out && c == 0) t_out[r] = *reinterpret_cast<const uint16_t *>(mr + kTByteF16B);
+}
+
+__global__ void import_f16b_kernel(const StateView st, int32_t n, const float *__restrict__ m_in,
+                                   const float *__restrict__ v_in, const uint32_t *__restrict__ t_in)
+{
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (int64_t)n * 8) return;
+    const int64_t r = gid / 8;
+    const int g = (int)(gid - r * 8);
+    int cols[8], cnt;
+    if (g < 6) {
+        cnt = 8;
+        for (int q = 0; q < 8; ++q) cols[q] = 11 + 8 * g + q;
+    } else if (g == 6) {
+        cnt = 4;
+        for (int q = 0; q < 4; ++q) cols[q] = 6 + q;
+    } else {
+        cnt = 7;
+        for (int q = 0; q < 6; ++q) cols[q] = q;
+        cols[6] = 10;
+    }
+    for (int side = 0; side < 2; ++side) {
+        const float *in = side ? v_in : m_in;
+        if (!in) continue;
+        char *row = static_cast<char *>(side ? st.v : st.m) + r * kRowBytesF16B;
+        float x[8];
+        for (int q = 0; q < cnt; ++q) x[q] = in[r * kNumCols + cols[q]];
+        const uint32_t e = group_exponent(x, cnt);
+        const float sc = e ? enc_scale(e) : 0.f;
+        for (int q = 0; q < cnt; ++q) {
+            int byte, group;
+            f16b_slot(cols[q], byte, group);
+            *reinterpret_cast<uint16_t *>(row + byte) = (uint16_t)(e ? h_bits(x[q] * sc) : 0u);
+        }
+        row[kF16BExp + g] = (char)e;
+    }
+    if (t_in && g == 7)
+        *reinterpret_cast<uint16_t *>(static_cast<char *>(st.m) + r * kRowBytesF16B + kTByteF16B) =
+            (uint16_t)min(t_in[r], 65535u);
+}
+
 // ----------------------------------------------------------- attribute gather
 // One thread per (output row, canonical column).
 // 16 lanes per output row: lanes 0-11 move the 12 float4 of the SH row,
@@ -340,6 +401,10 @@ cudaError_t launch_reindex(const StateView &in, int32_t n_in, const StateView &o
         reindex_kernel<10, kRowBytesHyb><<<blocks_for((int64_t)n_out * 10), kThreads, 0, s>>>(in, n_in, out, n_out,
                                                                                              src, reset, err);
         break;
+    case GS_MOM_FP16_BLOCK:
+        reindex_kernel<8, kRowBytesF16B><<<blocks_for((int64_t)n_out * 8), kThreads, 0, s>>>(in, n_in, out, n_out,
+                                                                                            src, reset, err);
+        break;
     default:
         return cudaErrorNotSupported;
     }
@@ -350,7 +415,10 @@ cudaError_t launch_export(const StateView &st, int32_t n, float *m_out, float *v
                           cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    export_kernel<<<blocks_for((int64_t)n * kNumCols), kThreads, 0, s>>>(st, n, m_out, v_out, t_out);
+    if (st.prec == GS_MOM_FP16_BLOCK)
+        export_f16b_kernel<<<blocks_for((int64_t)n * kNumCols), kThreads, 0, s>>>(st, n, m_out, v_out, t_out);
+    else
+        export_kernel<<<blocks_for((int64_t)n * kNumCols), kThreads, 0, s>>>(st, n, m_out, v_out, t_out);
     return cudaGetLastError();
 }
 
@@ -358,7 +426,10 @@ cudaError_t launch_import(const StateView &st, int32_t n, const float *m_in, con
                           const uint32_t *t_in, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    import_kernel<<<blocks_for((int64_t)n * kNumCols), kThreads, 0, s>>>(st, n, m_in, v_in, t_in);
+    if (st.prec == GS_MOM_FP16_BLOCK)
+        import_f16b_kernel<<<blocks_for((int64_t)n * 8), kThreads, 0, s>>>(st, n, m_in, v_in, t_in);
+    else
+        import_kernel<<<blocks_for((int64_t)n * kNumCols), kThreads, 0, s>>>(st, n, m_in, v_in, t_in);
     return cudaGetLastError();
 }
 

@@ -5,7 +5,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
-#include <cuda_fp8.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 #include "gsopt.h"
@@ -35,6 +35,10 @@ constexpr int kSlots = 64;
 constexpr int kRowBytesF32 = 256, kTByteF32 = 4 * 59;
 constexpr int kRowBytesBf16 = 128, kTByteBf16 = 120;
 constexpr int kRowBytesHyb = 160, kTByteHyb = 12, kHybShByte = 64;
+// GS_MOM_FP16_BLOCK rows (128 B): SH columns as FP16 at byte 2j (items of 8
+// columns at 16i), the 8 item exponents at 96 + item, rotation at 104,
+// xyz / scale / opacity at 112 .. 125, t (uint16) at 126.
+constexpr int kRowBytesF16B = 128, kTByteF16B = 126, kF16BExp = 96, kF16BRot = 104, kF16BXso = 112;
 constexpr int kSlotSh = 0, kSlotRot = 48, kSlotXyz = 52, kSlotScale = 55, kSlotOpacity = 58;
 constexpr int kSlotT = 59;
 constexpr int kNumCols = 59;
@@ -164,6 +168,33 @@ __device__ __forceinline__ float step_element(float th, float g, float &m, float
         else if (a.reg_mode == GS_REG_ADAMW_CLIP) u += fminf(lam * gr, clip);
     }
     return fmaf(-lr, u, th);
+}
+
+// GS_MOM_FP16_BLOCK encoding.  A group of values shares one exponent byte:
+// the largest biased FP32 exponent e among them (0 when every magnitude is
+// below 2^-112).  Values are stored as FP16 of x * 2^(141 - e), which puts
+// the largest magnitude in [2^14, 2^15).
+__device__ __forceinline__ uint32_t group_exponent(const float *x, int n)
+{
+    uint32_t e = 0;
+    for (int q = 0; q < n; ++q) e = max(e, (__float_as_uint(x[q]) >> 23) & 0xffu);
+    return e < 15u ? 0u : e;
+}
+// 2^(141 - e) and 2^(e - 141) as exact FP32 powers of two (15 <= e <= 254)
+__device__ __forceinline__ float enc_scale(uint32_t e) { return __uint_as_float((268u - e) << 23); }
+__device__ __forceinline__ float dec_scale(uint32_t e) { return e ? __uint_as_float((e - 14u) << 23) : 0.f; }
+
+__device__ __forceinline__ uint32_t h_bits(float y) { return __half_as_ushort(__float2half_rn(y)); }
+
+
+// Canonical column c -> byte offset of its FP16 value in an FP16-block row
+// and the index of its group exponent.
+__host__ __device__ inline void f16b_slot(int c, int &byte, int &group)
+{
+    if (c < 6) { byte = kF16BXso + 2 * c; group = 7; }                  // xyz, scale
+    else if (c < 10) { byte = kF16BRot + 2 * (c - 6); group = 6; }      // rotation
+    else if (c == 10) { byte = kF16BXso + 12; group = 7; }              // opacity
+    else { byte = 2 * (c - 11); group = (c - 11) / 8; }                 // SH
 }
 
 // Scene table of one batched launch (in device memory, written by one

@@ -278,6 +278,217 @@ struct State<GS_MOM_BF16_HYBRID> {
     }
 };
 
+// ------------------------------------------------------- FP16 with block exponents
+// Each work item's group of columns shares one exponent byte: the largest
+// biased FP32 exponent e among the group's values.  Values are stored as
+// FP16 of x * 2^(141 - e), which puts the largest magnitude in [2^14, 2^15);
+// every value within 2^29 of it is an FP16 normal with a 10-bit mantissa.
+// e < 15 (all magnitudes below 2^-112) stores zeros and e = 0.
+
+// FP32 -> FP16 bits rounded stochastically: 13 random bits added below the
+// 10 mantissa bits FP16 keeps, then truncated (exact in FP16 for normals).
+// FP16 subnormals (more than 2^29 below the group's maximum) round to nearest.
+__device__ __forceinline__ uint32_t h_bits_sr(float y, uint32_t rnd13)
+{
+    const uint32_t u = __float_as_uint(y);
+    if ((u & 0x7f800000u) < (113u << 23) || (u & 0x7f800000u) == 0x7f800000u) return h_bits(y);
+    return h_bits(__uint_as_float((u + (rnd13 & 0x1fffu)) & ~0x1fffu));
+}
+
+// n values -> FP16 bits (into h) and the group exponent; m to nearest, v
+// stochastically from hashes of (seed, iteration, row, first column).
+template <int n>
+__device__ __forceinline__ uint32_t encode_rn(const float *x, uint32_t *h)
+{
+    const uint32_t e = group_exponent(x, n);
+    const float s = e ? enc_scale(e) : 0.f;
+#pragma unroll
+    for (int q = 0; q < n; ++q) h[q] = e ? h_bits(x[q] * s) : 0u;
+    return e;
+}
+template <int n>
+__device__ __forceinline__ uint32_t encode_sr(const float *x, uint32_t *h, const StepArgs &a, int32_t r, int col0)
+{
+    const uint32_t e = group_exponent(x, n);
+    const float s = e ? enc_scale(e) : 0.f;
+#pragma unroll
+    for (int q = 0; q < n; q += 2) {
+        const uint32_t rnd = fmix32((uint32_t)r * 0x9e3779b1u ^ (uint32_t)(col0 + q) * 0x85ebca77u ^
+                                    (uint32_t)a.k_ctr * 0xc2b2ae3du ^ (uint32_t)a.seed ^ 0x165667b1u);
+        h[q] = e ? h_bits_sr(x[q] * s, rnd) : 0u;
+        if (q + 1 < n) h[q + 1] = e ? h_bits_sr(x[q + 1] * s, rnd >> 16) : 0u;
+    }
+    return e;
+}
+__device__ __forceinline__ float h_val(uint32_t bits16, float d)
+{
+    return __half2float(__ushort_as_half((unsigned short)(bits16 & 0xffffu))) * d;
+}
+
+template <>
+struct State<GS_MOM_FP16_BLOCK> {
+    static constexpr int kRowBytes = kRowBytesF16B, kTByte = kTByteF16B;
+    static constexpr bool kTInSh = false;
+    static __device__ __forceinline__ char *row(void *base, int32_t r)
+    {
+        return static_cast<char *>(base) + (size_t)r * kRowBytes;
+    }
+    template <int kW>
+    static __device__ __forceinline__ void load_sh(const StepArgs &a, int32_t r, int i, float *m, float *v, uint32_t &)
+    {
+        static_assert(kW == 8, "FP16 block items cover 8 SH columns");
+        const char *mr = row(a.m, r), *vr = row(a.v, r);
+        const uint4 um = *reinterpret_cast<const uint4 *>(mr + 16 * i), uv = *reinterpret_cast<const uint4 *>(vr + 16 * i);
+        const float dm = dec_scale((uint8_t)mr[kF16BExp + i]), dv = dec_scale((uint8_t)vr[kF16BExp + i]);
+        const uint32_t wm[4] = {um.x, um.y, um.z, um.w}, wv[4] = {uv.x, uv.y, uv.z, uv.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            m[2 * q] = h_val(wm[q], dm);
+            m[2 * q + 1] = h_val(wm[q] >> 16, dm);
+            v[2 * q] = h_val(wv[q], dv);
+            v[2 * q + 1] = h_val(wv[q] >> 16, dv);
+        }
+    }
+    template <int kW>
+    static __device__ __forceinline__ void store_sh(const StepArgs &a, int32_t r, int i, const float *m,
+                                                    const float *v, uint32_t)
+    {
+        char *mr = row(a.m, r), *vr = row(a.v, r);
+        uint32_t hm[8], hv[8];
+        const uint32_t em = encode_rn<8>(m, hm), ev = encode_sr<8>(v, hv, a, r, 11 + 8 * i);
+        __stcs(reinterpret_cast<uint4 *>(mr + 16 * i), make_uint4(hm[0] | hm[1] << 16, hm[2] | hm[3] << 16,
+                                                                  hm[4] | hm[5] << 16, hm[6] | hm[7] << 16));
+        __stcs(reinterpret_cast<uint4 *>(vr + 16 * i), make_uint4(hv[0] | hv[1] << 16, hv[2] | hv[3] << 16,
+                                                                  hv[4] | hv[5] << 16, hv[6] | hv[7] << 16));
+        mr[kF16BExp + i] = (char)em;
+        vr[kF16BExp + i] = (char)ev;
+    }
+};
+
+// The small columns of an FP16-block row in two items: c = 12 rotation (4
+// values at kF16BRot, exponent 6), c = 13 xyz + scale + opacity (7 values at
+// kF16BXso, exponent 7) with the step count t (uint16, saturating) beside
+// them.  The visible update as small_item; RSR scales the moments afterwards.
+__device__ __forceinline__ void small_item_f16b(const StepArgs &a, const int32_t row, const int c, const bool sampled,
+                                                const float2 f)
+{
+    using S = State<GS_MOM_FP16_BLOCK>;
+    char *mr = S::row(a.m, row), *vr = S::row(a.v, row);
+    const size_t r = (size_t)row;
+    if (c == 12) {
+        const uint2 um = *reinterpret_cast<const uint2 *>(mr + kF16BRot), uv = *reinterpret_cast<const uint2 *>(vr + kF16BRot);
+        const float dm = dec_scale((uint8_t)mr[kF16BExp + 6]), dv = dec_scale((uint8_t)vr[kF16BExp + 6]);
+        float m[4] = {h_val(um.x, dm), h_val(um.x >> 16, dm), h_val(um.y, dm), h_val(um.y >> 16, dm)};
+        float v[4] = {h_val(uv.x, dv), h_val(uv.x >> 16, dv), h_val(uv.y, dv), h_val(uv.y >> 16, dv)};
+        float *pt = a.a_rot + r * 4;
+        float4 th = ld4(pt);
+        const float4 g = ldg4_stream(a.g_rot + r * 4);
+        const float l = a.lr[2];
+        th.x = step_element(th.x, g.x, m[0], v[0], f.x, f.y, a, l, false, 0.f, 0.f, 0.f);
+        th.y = step_element(th.y, g.y, m[1], v[1], f.x, f.y, a, l, false, 0.f, 0.f, 0.f);
+        th.z = step_element(th.z, g.z, m[2], v[2], f.x, f.y, a, l, false, 0.f, 0.f, 0.f);
+        th.w = step_element(th.w, g.w, m[3], v[3], f.x, f.y, a, l, false, 0.f, 0.f, 0.f);
+        st4(pt, th);
+        if (sampled) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                m[q] *= a.alpha1;
+                v[q] *= a.alpha2;
+            }
+        }
+        uint32_t hm[4], hv[4];
+        const uint32_t em = encode_rn<4>(m, hm), ev = encode_sr<4>(v, hv, a, row, 6);
+        __stcs(reinterpret_cast<uint2 *>(mr + kF16BRot), make_uint2(hm[0] | hm[1] << 16, hm[2] | hm[3] << 16));
+        __stcs(reinterpret_cast<uint2 *>(vr + kF16BRot), make_uint2(hv[0] | hv[1] << 16, hv[2] | hv[3] << 16));
+        mr[kF16BExp + 6] = (char)em;
+        vr[kF16BExp + 6] = (char)ev;
+    } else {
+        const uint4 um = *reinterpret_cast<const uint4 *>(mr + kF16BXso), uv = *reinterpret_cast<const uint4 *>(vr + kF16BXso);
+        const float dm = dec_scale((uint8_t)mr[kF16BExp + 7]), dv = dec_scale((uint8_t)vr[kF16BExp + 7]);
+        const uint32_t wm[4] = {um.x, um.y, um.z, um.w}, wv[4] = {uv.x, uv.y, uv.z, uv.w};
+        float m[7], v[7];
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+            m[q] = h_val(wm[q / 2] >> (16 * (q & 1)), dm);
+            v[q] = h_val(wv[q / 2] >> (16 * (q & 1)), dv);
+        }
+        uint32_t t = um.w >> 16;
+        float *px = a.a_xyz + r * 3, *ps = a.a_scale + r * 3, *po = a.a_op + r;
+        float x0 = px[0], x1 = px[1], x2 = px[2], s0 = ps[0], s1 = ps[1], s2 = ps[2], op = *po;
+        const float *gx = a.g_xyz + r * 3, *gs = a.g_scale + r * 3;
+        const float g0 = __ldcs(gx), g1 = __ldcs(gx + 1), g2 = __ldcs(gx + 2);
+        const float gs0 = __ldcs(gs), gs1 = __ldcs(gs + 1), gs2 = __ldcs(gs + 2), go = __ldcs(a.g_op + r);
+        const bool ds = a.dar_s != 0, dop = a.dar_o != 0;
+        // regulariser derivatives at the old values (App. Eqs. scale, opacity)
+        const float r0s = ds ? expf(s0) : 0.f, r1s = ds ? expf(s1) : 0.f, r2s = ds ? expf(s2) : 0.f;
+        const float rop = dop ? dsigmoid(op) : 0.f;
+        x0 = step_element(x0, g0, m[0], v[0], f.x, f.y, a, a.lr[0], false, 0.f, 0.f, 0.f);
+        x1 = step_element(x1, g1, m[1], v[1], f.x, f.y, a, a.lr[0], false, 0.f, 0.f, 0.f);
+        x2 = step_element(x2, g2, m[2], v[2], f.x, f.y, a, a.lr[0], false, 0.f, 0.f, 0.f);
+        s0 = step_element(s0, gs0, m[3], v[3], f.x, f.y, a, a.lr[1], ds, r0s, a.lam_s, a.clip_s);
+        s1 = step_element(s1, gs1, m[4], v[4], f.x, f.y, a, a.lr[1], ds, r1s, a.lam_s, a.clip_s);
+        s2 = step_element(s2, gs2, m[5], v[5], f.x, f.y, a, a.lr[1], ds, r2s, a.lam_s, a.clip_s);
+        op = step_element(op, go, m[6], v[6], f.x, f.y, a, a.lr[3], dop, rop, a.lam_o, a.clip_o);
+        __stcs(px, x0); __stcs(px + 1, x1); __stcs(px + 2, x2);
+        __stcs(ps, s0); __stcs(ps + 1, s1); __stcs(ps + 2, s2);
+        __stcs(po, op);
+        t = min(t + 1u, 65535u);                    // the row's own step count (Sec. 3.2)
+        if (sampled) {
+#pragma unroll
+            for (int q = 0; q < 7; ++q) {
+                m[q] *= a.alpha1;
+                v[q] *= a.alpha2;
+            }
+        }
+        uint32_t hm[7], hv[7];
+        const uint32_t em = encode_rn<7>(m, hm), ev = encode_sr<7>(v, hv, a, row, 0);
+        __stcs(reinterpret_cast<uint4 *>(mr + kF16BXso), make_uint4(hm[0] | hm[1] << 16, hm[2] | hm[3] << 16,
+                                                                   hm[4] | hm[5] << 16, hm[6] | t << 16));
+        __stcs(reinterpret_cast<uint4 *>(vr + kF16BXso), make_uint4(hv[0] | hv[1] << 16, hv[2] | hv[3] << 16,
+                                                                   hv[4] | hv[5] << 16, hv[6]));
+        mr[kF16BExp + 7] = (char)em;
+        vr[kF16BExp + 7] = (char)ev;
+    }
+}
+
+// RSR of one small item of an invisible FP16-block row (moments only, t kept).
+__device__ __forceinline__ void rsr_small_f16b(const StepArgs &a, const int32_t row, const int c)
+{
+    using S = State<GS_MOM_FP16_BLOCK>;
+    char *mr = S::row(a.m, row), *vr = S::row(a.v, row);
+    if (c == 12) {
+        const uint2 um = *reinterpret_cast<const uint2 *>(mr + kF16BRot), uv = *reinterpret_cast<const uint2 *>(vr + kF16BRot);
+        const float dm = dec_scale((uint8_t)mr[kF16BExp + 6]) * a.alpha1, dv = dec_scale((uint8_t)vr[kF16BExp + 6]) * a.alpha2;
+        float m[4] = {h_val(um.x, dm), h_val(um.x >> 16, dm), h_val(um.y, dm), h_val(um.y >> 16, dm)};
+        float v[4] = {h_val(uv.x, dv), h_val(uv.x >> 16, dv), h_val(uv.y, dv), h_val(uv.y >> 16, dv)};
+        uint32_t hm[4], hv[4];
+        const uint32_t em = encode_rn<4>(m, hm), ev = encode_sr<4>(v, hv, a, row, 6);
+        __stcs(reinterpret_cast<uint2 *>(mr + kF16BRot), make_uint2(hm[0] | hm[1] << 16, hm[2] | hm[3] << 16));
+        __stcs(reinterpret_cast<uint2 *>(vr + kF16BRot), make_uint2(hv[0] | hv[1] << 16, hv[2] | hv[3] << 16));
+        mr[kF16BExp + 6] = (char)em;
+        vr[kF16BExp + 6] = (char)ev;
+    } else {
+        const uint4 um = *reinterpret_cast<const uint4 *>(mr + kF16BXso), uv = *reinterpret_cast<const uint4 *>(vr + kF16BXso);
+        const float dm = dec_scale((uint8_t)mr[kF16BExp + 7]) * a.alpha1, dv = dec_scale((uint8_t)vr[kF16BExp + 7]) * a.alpha2;
+        const uint32_t wm[4] = {um.x, um.y, um.z, um.w}, wv[4] = {uv.x, uv.y, uv.z, uv.w};
+        float m[7], v[7];
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+            m[q] = h_val(wm[q / 2] >> (16 * (q & 1)), dm);
+            v[q] = h_val(wv[q / 2] >> (16 * (q & 1)), dv);
+        }
+        const uint32_t t = um.w >> 16;
+        uint32_t hm[7], hv[7];
+        const uint32_t em = encode_rn<7>(m, hm), ev = encode_sr<7>(v, hv, a, row, 0);
+        __stcs(reinterpret_cast<uint4 *>(mr + kF16BXso), make_uint4(hm[0] | hm[1] << 16, hm[2] | hm[3] << 16,
+                                                                   hm[4] | hm[5] << 16, hm[6] | t << 16));
+        __stcs(reinterpret_cast<uint4 *>(vr + kF16BXso), make_uint4(hv[0] | hv[1] << 16, hv[2] | hv[3] << 16,
+                                                                   hv[4] | hv[5] << 16, hv[6]));
+        mr[kF16BExp + 7] = (char)em;
+        vr[kF16BExp + 7] = (char)ev;
+    }
+}
+
 // Ask L2 to fetch the contiguous parts a visible row's items will read (SH
 // attributes and gradients, m and v rows; cp.async.bulk.prefetch.L2), as
 // soon as the row is known to be visible.  Worth it for sparse tiles: their
@@ -299,6 +510,11 @@ __device__ __forceinline__ void prefetch_row_l2(const StepArgs &a, int32_t row)
 // Prefetch when at most 60 % of the tile's rows are visible.
 template <int kTile>
 __device__ __forceinline__ bool sparse_tile(int nv) { return 5 * nv <= 3 * kTile; }
+
+// Small items per row: rotation; xyz + scale0; scale1 + scale2 + opacity,
+// except FP16-block rows (rotation; xyz + scale + opacity).
+template <int kPrec>
+constexpr int kSmallItems = kPrec == GS_MOM_FP16_BLOCK ? 2 : 3;
 
 // ---------------------------------------------------------------- the items
 
@@ -344,61 +560,65 @@ template <int kPrec>
 __device__ __forceinline__ void small_item(const StepArgs &a, const int32_t row, const int c, const bool sampled,
                                            const float2 f)
 {
-    using S = State<kPrec>;
-    Chunk k = S::load_small(a, row, c);
-    float4 &m = k.m, &v = k.v;
-    const size_t r = (size_t)row;
-    if (c == 12) {
-        // rotation quaternion
-        float *pt = a.a_rot + r * 4;
-        float4 th = ld4(pt);
-        const float4 g = ldg4_stream(a.g_rot + r * 4);
-        const float l = a.lr[2];
-        th.x = step_element(th.x, g.x, m.x, v.x, f.x, f.y, a, l, false, 0.f, 0.f, 0.f);
-        th.y = step_element(th.y, g.y, m.y, v.y, f.x, f.y, a, l, false, 0.f, 0.f, 0.f);
-        th.z = step_element(th.z, g.z, m.z, v.z, f.x, f.y, a, l, false, 0.f, 0.f, 0.f);
-        th.w = step_element(th.w, g.w, m.w, v.w, f.x, f.y, a, l, false, 0.f, 0.f, 0.f);
-        st4(pt, th);
-    } else if (c == 13) {
-        // xyz and the first log-scale component
-        float *px = a.a_xyz + r * 3;
-        float *ps = a.a_scale + r * 3;
-        const float *gx = a.g_xyz + r * 3;
-        float x0 = px[0], x1 = px[1], x2 = px[2], s0 = ps[0];
-        const float g0 = __ldcs(gx), g1 = __ldcs(gx + 1), g2 = __ldcs(gx + 2), gs0 = __ldcs(a.g_scale + r * 3);
-        const bool ds = a.dar_s != 0;
-        // scale: dR/dkappa = exp(kappa) at the old value (App. Eq. scale)
-        const float r0s = ds ? expf(s0) : 0.f;
-        x0 = step_element(x0, g0, m.x, v.x, f.x, f.y, a, a.lr[0], false, 0.f, 0.f, 0.f);
-        x1 = step_element(x1, g1, m.y, v.y, f.x, f.y, a, a.lr[0], false, 0.f, 0.f, 0.f);
-        x2 = step_element(x2, g2, m.z, v.z, f.x, f.y, a, a.lr[0], false, 0.f, 0.f, 0.f);
-        s0 = step_element(s0, gs0, m.w, v.w, f.x, f.y, a, a.lr[1], ds, r0s, a.lam_s, a.clip_s);
-        __stcs(px, x0); __stcs(px + 1, x1); __stcs(px + 2, x2);
-        __stcs(ps, s0);
+    if constexpr (kPrec == GS_MOM_FP16_BLOCK) {
+        small_item_f16b(a, row, c, sampled, f);
     } else {
-        // the other two log-scale components and the opacity logit
-        float *ps = a.a_scale + r * 3;
-        float *po = a.a_op + r;
-        const float *gsp = a.g_scale + r * 3;
-        float s1 = ps[1], s2 = ps[2], op = *po;
-        const float gs1 = __ldcs(gsp + 1), gs2 = __ldcs(gsp + 2), go = __ldcs(a.g_op + r);
-        const bool ds = a.dar_s != 0, dop = a.dar_o != 0;
-        const float r1s = ds ? expf(s1) : 0.f, r2s = ds ? expf(s2) : 0.f;
-        // opacity: dR/dtau = sig'(tau) at the old value (App. Eq. opacity)
-        const float rop = dop ? dsigmoid(op) : 0.f;
-        s1 = step_element(s1, gs1, m.x, v.x, f.x, f.y, a, a.lr[1], ds, r1s, a.lam_s, a.clip_s);
-        s2 = step_element(s2, gs2, m.y, v.y, f.x, f.y, a, a.lr[1], ds, r2s, a.lam_s, a.clip_s);
-        op = step_element(op, go, m.z, v.z, f.x, f.y, a, a.lr[3], dop, rop, a.lam_o, a.clip_o);
-        __stcs(ps + 1, s1); __stcs(ps + 2, s2);
-        __stcs(po, op);
-        if (!S::kTInSh) k.t += 1u;         // the row's own step count (Sec. 3.2)
+        using S = State<kPrec>;
+        Chunk k = S::load_small(a, row, c);
+        float4 &m = k.m, &v = k.v;
+        const size_t r = (size_t)row;
+        if (c == 12) {
+            // rotation quaternion
+            float *pt = a.a_rot + r * 4;
+            float4 th = ld4(pt);
+            const float4 g = ldg4_stream(a.g_rot + r * 4);
+            const float l = a.lr[2];
+            th.x = step_element(th.x, g.x, m.x, v.x, f.x, f.y, a, l, false, 0.f, 0.f, 0.f);
+            th.y = step_element(th.y, g.y, m.y, v.y, f.x, f.y, a, l, false, 0.f, 0.f, 0.f);
+            th.z = step_element(th.z, g.z, m.z, v.z, f.x, f.y, a, l, false, 0.f, 0.f, 0.f);
+            th.w = step_element(th.w, g.w, m.w, v.w, f.x, f.y, a, l, false, 0.f, 0.f, 0.f);
+            st4(pt, th);
+        } else if (c == 13) {
+            // xyz and the first log-scale component
+            float *px = a.a_xyz + r * 3;
+            float *ps = a.a_scale + r * 3;
+            const float *gx = a.g_xyz + r * 3;
+            float x0 = px[0], x1 = px[1], x2 = px[2], s0 = ps[0];
+            const float g0 = __ldcs(gx), g1 = __ldcs(gx + 1), g2 = __ldcs(gx + 2), gs0 = __ldcs(a.g_scale + r * 3);
+            const bool ds = a.dar_s != 0;
+            // scale: dR/dkappa = exp(kappa) at the old value (App. Eq. scale)
+            const float r0s = ds ? expf(s0) : 0.f;
+            x0 = step_element(x0, g0, m.x, v.x, f.x, f.y, a, a.lr[0], false, 0.f, 0.f, 0.f);
+            x1 = step_element(x1, g1, m.y, v.y, f.x, f.y, a, a.lr[0], false, 0.f, 0.f, 0.f);
+            x2 = step_element(x2, g2, m.z, v.z, f.x, f.y, a, a.lr[0], false, 0.f, 0.f, 0.f);
+            s0 = step_element(s0, gs0, m.w, v.w, f.x, f.y, a, a.lr[1], ds, r0s, a.lam_s, a.clip_s);
+            __stcs(px, x0); __stcs(px + 1, x1); __stcs(px + 2, x2);
+            __stcs(ps, s0);
+        } else {
+            // the other two log-scale components and the opacity logit
+            float *ps = a.a_scale + r * 3;
+            float *po = a.a_op + r;
+            const float *gsp = a.g_scale + r * 3;
+            float s1 = ps[1], s2 = ps[2], op = *po;
+            const float gs1 = __ldcs(gsp + 1), gs2 = __ldcs(gsp + 2), go = __ldcs(a.g_op + r);
+            const bool ds = a.dar_s != 0, dop = a.dar_o != 0;
+            const float r1s = ds ? expf(s1) : 0.f, r2s = ds ? expf(s2) : 0.f;
+            // opacity: dR/dtau = sig'(tau) at the old value (App. Eq. opacity)
+            const float rop = dop ? dsigmoid(op) : 0.f;
+            s1 = step_element(s1, gs1, m.x, v.x, f.x, f.y, a, a.lr[1], ds, r1s, a.lam_s, a.clip_s);
+            s2 = step_element(s2, gs2, m.y, v.y, f.x, f.y, a, a.lr[1], ds, r2s, a.lam_s, a.clip_s);
+            op = step_element(op, go, m.z, v.z, f.x, f.y, a, a.lr[3], dop, rop, a.lam_o, a.clip_o);
+            __stcs(ps + 1, s1); __stcs(ps + 2, s2);
+            __stcs(po, op);
+            if (!S::kTInSh) k.t += 1u;         // the row's own step count (Sec. 3.2)
+        }
+        if (sampled) {         // RSR post-scale (chunk 14 holds 3 moments)
+            m.x *= a.alpha1; m.y *= a.alpha1; m.z *= a.alpha1;
+            v.x *= a.alpha2; v.y *= a.alpha2; v.z *= a.alpha2;
+            if (c != 14) { m.w *= a.alpha1; v.w *= a.alpha2; }
+        }
+        S::store_small(a, row, c, k);
     }
-    if (sampled) {         // RSR post-scale (chunk 14 holds 3 moments)
-        m.x *= a.alpha1; m.y *= a.alpha1; m.z *= a.alpha1;
-        v.x *= a.alpha2; v.y *= a.alpha2; v.z *= a.alpha2;
-        if (c != 14) { m.w *= a.alpha1; v.w *= a.alpha2; }
-    }
-    S::store_small(a, row, c, k);
 }
 
 // RSR (Eq. meth::restate) of an invisible StSS-sampled row: SH item i
@@ -418,6 +638,8 @@ __device__ __forceinline__ void rsr_item(const StepArgs &a, const int32_t row, c
             v[e] *= a.alpha2;
         }
         S::template store_sh<kW>(a, row, i, m, v, t);
+    } else if constexpr (kPrec == GS_MOM_FP16_BLOCK) {
+        rsr_small_f16b(a, row, 12 + (i - kNsh));
     } else {
         const int c = 12 + (i - kNsh);
         Chunk k = S::load_small(a, row, c);

@@ -67,9 +67,11 @@ __device__ __forceinline__ void tile_decide(const StepArgs &a, const int vis_src
             } else {
                 vis = true;
             }
-            if (vis && !a.bias_mode)
-                t_old[j] = *reinterpret_cast<const uint32_t *>(static_cast<const char *>(a.m) +
-                                                               (size_t)row * kRowBytes + kTByte);
+            if (vis && !a.bias_mode) {
+                const char *tp = static_cast<const char *>(a.m) + (size_t)row * kRowBytes + kTByte;
+                if constexpr (kTByte % 4 == 0) t_old[j] = *reinterpret_cast<const uint32_t *>(tp);
+                else t_old[j] = *reinterpret_cast<const uint16_t *>(tp);      // FP16-block rows: uint16 t
+            }
             if (a.mask_out) a.mask_out[row] = vis ? 1 : 0;
             if (a.restate) smp = stss_sampled(a, (int32_t)row);
         }
@@ -123,7 +125,7 @@ __device__ __forceinline__ void process_tile(const StepArgs &a, const int vis_sr
     static_assert(kTile % kThreads == 0, "tile must be a multiple of the block");
     static_assert(kW == 4 || kW == 8, "SH items cover 4 or 8 columns");
     using S = State<kPrec>;
-    constexpr int kNsh = 48 / kW, kItems = kNsh + 3;
+    constexpr int kNsh = 48 / kW, kItems = kNsh + kSmallItems<kPrec>;
     int nv, nr;
     tile_decide<kTile, S::kRowBytes, S::kTByte>(a, vis_src, r0, L, nv, nr);
 
@@ -218,6 +220,9 @@ cudaError_t launch_step(const StepArgs &a, int prec, int vis_src, cudaStream_t s
         break;
     case GS_MOM_BF16_HYBRID:
         step_tile<kStepTile, kStepMinBlocks, GS_MOM_BF16_HYBRID, kShWBf16><<<grid, kThreads, 0, s>>>(a, vis_src);
+        break;
+    case GS_MOM_FP16_BLOCK:
+        step_tile<kStepTile, kStepMinBlocks, GS_MOM_FP16_BLOCK, 8><<<grid, kThreads, 0, s>>>(a, vis_src);
         break;
     default:
         return cudaErrorNotSupported;

@@ -16,7 +16,7 @@ _LIB_PATH = Path(__file__).resolve().parent / "libgsopt.so"
 _lib = None
 
 GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CUDA, GS_ERR_OOM, GS_ERR_UNSUPPORTED, GS_ERR_TIMEOUT, GS_ERR_STATE = range(7)
-GS_MOM_FP32, GS_MOM_BF16, GS_MOM_FP8E4M3, GS_MOM_BF16_HYBRID = range(4)
+GS_MOM_FP32, GS_MOM_BF16, GS_MOM_FP8E4M3, GS_MOM_BF16_HYBRID, GS_MOM_FP16_BLOCK = range(5)
 GS_REG_DAR, GS_REG_COUPLED, GS_REG_ADAMW, GS_REG_ADAMW_CLIP = range(4)
 GS_NOISE_OFF, GS_NOISE_VISIBLE, GS_NOISE_ALL = range(3)
 GROUPS = (("xyz", 3), ("scale", 3), ("rot", 4), ("opacity", 1), ("sh", 48))

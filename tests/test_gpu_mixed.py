@@ -1,11 +1,14 @@
-"""Low-precision moment storage (GS_MOM_BF16, GS_MOM_BF16_HYBRID) against the
-FP64 oracle.
+"""Low-precision moment storage (GS_MOM_BF16, GS_MOM_BF16_HYBRID,
+GS_MOM_FP16_BLOCK) against the FP64 oracle.
 
 Bounds, from the arithmetic: the step computes every moment in FP32 and only
 rounds the stored copy, so after one step from zero state the attributes are
 as accurate as the FP32 path and each stored moment is within BF16's rounding
 of the oracle's: half an ulp (2^-8 relative) when rounded to nearest, one ulp
-(2^-7) when rounded stochastically (the hybrid's SH second moments).  Over
+(2^-7) when rounded stochastically (the hybrid's SH second moments).  For
+FP16 blocks the ulp is 2^-10 relative for every value within 2^29 of its
+group's largest magnitude; below that FP16 subnormals space values 2^-24
+apart in the group's scaled units.  Over
 many steps the rounded moments feed back; after 1000 steps of the 3 M
 workload the metric's gate, group relative L2 ||d|| / ||theta_ref|| <= 1e-3,
 is asserted for the hybrid.  All-BF16 misses it (its second moments move
@@ -26,6 +29,10 @@ if not torch.cuda.is_available():
 
 LR = synth.lr_for_step(1, 10)
 BF16_HALF_ULP = 2.0 ** -8
+FP16_HALF_ULP = 2.0 ** -11
+# FP16-block groups in canonical columns: 6 x 8 SH, rotation, xyz + scale + opacity
+F16B_GROUPS = [list(range(11 + 8 * g, 19 + 8 * g)) for g in range(6)] + [[6, 7, 8, 9], [0, 1, 2, 3, 4, 5, 10]]
+LOWP = ["BF16", "BF16_HYBRID", "FP16_BLOCK"]
 GROUP_COLS = {"xyz": slice(0, 3), "scale": slice(3, 6), "rot": slice(6, 10), "opacity": slice(10, 11),
               "sh": slice(11, 59)}
 
@@ -42,6 +49,34 @@ def _bf16(x):
     return torch.from_numpy(np.ascontiguousarray(x, np.float32)).to(torch.bfloat16).to(torch.float32).numpy()
 
 
+def _group_exponent(blk):
+    e = ((np.ascontiguousarray(blk, np.float32).view(np.uint32) >> 23) & 0xFF).max(axis=1).astype(np.int64)
+    return np.where(e < 15, 0, e)
+
+
+def _f16b(x):
+    """The FP16-block encoding restated: per row and group, the largest biased
+    FP32 exponent e; values stored as FP16 (nearest) of x * 2^(141 - e)."""
+    x = np.ascontiguousarray(x, np.float32)
+    out = np.zeros_like(x)
+    for cols in F16B_GROUPS:
+        blk = x[:, cols].astype(np.float64)
+        e = _group_exponent(x[:, cols])
+        sc = np.where(e > 0, np.ldexp(1.0, 141 - e), 0.0)
+        h = (blk * sc[:, None]).astype(np.float32).astype(np.float16)
+        dec = np.where(e > 0, np.ldexp(1.0, e - 141), 0.0)
+        out[:, cols] = (h.astype(np.float64) * dec[:, None]).astype(np.float32)
+    return out
+
+
+def _group_max(x):
+    """Per element, the largest magnitude of its FP16-block group."""
+    out = np.zeros(x.shape, np.float64)
+    for cols in F16B_GROUPS:
+        out[:, cols] = np.abs(x[:, cols]).max(axis=1, keepdims=True)
+    return out
+
+
 def group_rel_l2(got, ref, rows=None):
     out = {}
     for g, sl in GROUP_COLS.items():
@@ -53,7 +88,7 @@ def group_rel_l2(got, ref, rows=None):
     return out
 
 
-@pytest.mark.parametrize("prec", ["BF16", "BF16_HYBRID"])
+@pytest.mark.parametrize("prec", LOWP)
 def test_one_step(G, orc, prec):
     n = 60_013
     groups = synth.scene_blobs(n, 901, 12.5)
@@ -68,10 +103,12 @@ def test_one_step(G, orc, prec):
     vis = ref.visible(cam)
     ref.step(grads, vis, LR, True, True, 100, restate=True, ratio=0.3, seed=9)
     assert_close(got, ref.st.theta, 1e-5, 1e-5, what="theta")
-    v_ulps = 2.0 if prec == "BF16_HYBRID" else 1.0       # stochastic rounding: within one ulp
+    v_ulps = 1.0 if prec == "BF16" else 2.0              # stochastic rounding: within one ulp
+    half = FP16_HALF_ULP if prec == "FP16_BLOCK" else BF16_HALF_ULP
     for name, a, b, ulps in [("m", m, ref.st.m, 1.0), ("v", v, ref.st.v, v_ulps)]:
         d = np.abs(a - b)
-        assert np.all(d <= ulps * BF16_HALF_ULP * np.abs(b) * (1 + 1e-5) + 1e-30), f"{name} beyond BF16 rounding"
+        floor = 2.0 ** -37 * _group_max(b) if prec == "FP16_BLOCK" else 0.0     # FP16 subnormal spacing
+        assert np.all(d <= ulps * half * np.abs(b) * (1 + 1e-5) + floor + 1e-30), f"{name} beyond {prec} rounding"
     if prec == "BF16_HYBRID":      # columns 0-13 (all but the SH rest) stay FP32
         assert_close(m[:, :14], ref.st.m[:, :14], 1e-5)
         assert_close(v[:, :14], ref.st.v[:, :14], 1e-5)
@@ -79,7 +116,7 @@ def test_one_step(G, orc, prec):
     run.close()
 
 
-@pytest.mark.parametrize("prec", ["BF16", "BF16_HYBRID"])
+@pytest.mark.parametrize("prec", LOWP)
 @pytest.mark.parametrize("n", [1, 33, 257, 513])
 def test_edge_sizes(G, orc, prec, n):
     groups = synth.scene_uniform(n, 910 + n)
@@ -100,7 +137,7 @@ def test_edge_sizes(G, orc, prec, n):
     run.close()
 
 
-@pytest.mark.parametrize("prec", ["BF16", "BF16_HYBRID"])
+@pytest.mark.parametrize("prec", LOWP)
 def test_export_import_and_reindex(G, orc, prec):
     n = 20_001
     run = GpuRun(synth.scene_uniform(n, 920), prec=getattr(G, "GS_MOM_" + prec))
@@ -111,7 +148,10 @@ def test_export_import_and_reindex(G, orc, prec):
     G.gs_opt_import_state(run.h, torch.from_numpy(m).cuda(), torch.from_numpy(v).cuda(),
                           torch.from_numpy(t.view(np.int32)).cuda())
     m2, v2, t2 = run.state()
-    em, ev = _bf16(m), _bf16(v)
+    if prec == "FP16_BLOCK":
+        em, ev = _f16b(m), _f16b(v)
+    else:
+        em, ev = _bf16(m), _bf16(v)
     if prec == "BF16_HYBRID":
         em[:, :14], ev[:, :14] = m[:, :14], v[:, :14]
     assert m2.tobytes() == em.tobytes() and v2.tobytes() == ev.tobytes() and t2.tobytes() == t.tobytes()
@@ -153,7 +193,7 @@ def _run_sampled(G, orc, wl, prec, sample):
     return got, ref.st.theta, ~diverged
 
 
-@pytest.mark.parametrize("prec,gate", [("BF16_HYBRID", 1e-3), ("BF16", 3e-2)])
+@pytest.mark.parametrize("prec,gate", [("FP16_BLOCK", 1e-3), ("BF16_HYBRID", 1e-3), ("BF16", 3e-2)])
 def test_3m_1000_steps_sampled(G, orc, prec, gate):
     """The 3 M-primitive, 1000-step workload (about 20 % visible per view),
     followed by the oracle on 2000 sampled primitives."""
@@ -165,3 +205,24 @@ def test_3m_1000_steps_sampled(G, orc, prec, gate):
     print(prec, "group relative L2 after 1000 steps:", errs)
     for g, e in errs.items():
         assert e <= gate, f"{prec} group {g}: {e:.2e} > {gate:.0e}"
+
+
+def test_fp16_block_rejects_optional_terms_and_batches(G):
+    """FP16-block moments have no extended-step or batched variant: those
+    requests are refused before anything is launched, and the context stays
+    usable."""
+    n = 1000
+    run = GpuRun(synth.scene_uniform(n, 930), prec=G.GS_MOM_FP16_BLOCK)
+    mask = torch.ones(n, dtype=torch.uint8, device="cuda")
+    na = torch.zeros(1, dtype=torch.int64, device="cuda")
+    for kw in (dict(noise=1), dict(aiu=True, aiu_prob=0.1), dict(n_active=na)):
+        with pytest.raises(G.GsError) as e:
+            run.step_mask(mask, G.make_params(LR, 1, **kw))
+        assert e.value.status == G.GS_ERR_UNSUPPORTED
+    with pytest.raises(G.GsError) as e:
+        G.gs_batch_create([run.h])
+    assert e.value.status == G.GS_ERR_UNSUPPORTED
+    run.step_mask(mask, G.make_params(LR, 1))         # the plain step still runs
+    torch.cuda.synchronize()
+    assert G.gs_opt_sync_errors(run.h) == G.GS_OK
+    run.close()
