@@ -70,7 +70,7 @@ typedef enum gs_status {
  * learning rate relative to its magnitude.  Measured group errors after 1000
  * steps of the 3 M-primitive workload against the FP64 reference are
  * reported by the tests and the bench (GS_MOM_BF16: about 1e-2 on opacity;
- * GS_MOM_BF16_HYBRID: below 1e-3 in every group). */
+ * GS_MOM_BF16_HYBRID: 3e-4; GS_MOM_FP16_BLOCK: 6e-4). */
 typedef enum gs_moment_prec {
     GS_MOM_FP32 = 0,
     GS_MOM_BF16 = 1,        /* all 59 columns BF16, round-to-nearest-even             */
