@@ -281,11 +281,14 @@ gs_status gs_step_camera(gs_opt *opt, const gs_attrs *attrs, const gs_grads *gra
                          const gs_step_params *params, void *stream);
 
 /*
- * gs_step_camera with the gradients in HOST memory: copies the five gradient
- * groups into a library-owned device staging buffer on `stream`, runs the
- * fused step, copies the visible count back to *n_visible_host and
- * synchronises `stream` before returning (blocking).  Pinned host memory
- * makes the copies run at full link speed.
+ * gs_step_camera with the gradients in HOST memory; copies the visible count
+ * back to *n_visible_host and synchronises `stream` before returning
+ * (blocking).  When all five gradient groups are pinned host memory the
+ * device can address (cudaHostAlloc / cudaHostRegister under unified
+ * addressing; rot and sh 16-byte aligned), the step kernel reads the visible
+ * rows' gradients in place over the CPU-GPU link and nothing else is copied.
+ * Otherwise the groups are first copied into a library-owned device staging
+ * buffer on `stream` (allocated on first use).  Both give the same result.
  */
 gs_status gs_step_host(gs_opt *opt, const gs_attrs *attrs, const gs_grads *grads_host,
                        const gs_camera *cam, const gs_step_params *params,

@@ -279,6 +279,19 @@ void set_attrs(StepArgs *a, const gs_attrs *x, const A *g)
     a->g_xyz = g->xyz; a->g_scale = g->scale; a->g_rot = g->rot; a->g_op = g->opacity; a->g_sh = g->sh;
 }
 
+// Pinned host memory the device can address (mapped, unified addressing):
+// the device-side address of p, or nullptr.
+const float *mapped_host(const float *p, size_t align)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (at.type != cudaMemoryTypeHost || !at.devicePointer || (uintptr_t)at.devicePointer % align) return nullptr;
+    return static_cast<const float *>(at.devicePointer);
+}
+
 }  // namespace
 
 extern "C" {
@@ -452,6 +465,37 @@ gs_status gs_step_host(gs_opt *o, const gs_attrs *attrs, const gs_grads *gh, con
     if (n && (!gh->xyz || !gh->scale || !gh->rot || !gh->opacity || !gh->sh)) return GS_ERR_INVALID_ARG;
     if (!attrs_ok(o, *attrs, n)) return GS_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!o->count) {
+        if (cudaMalloc(&o->count, sizeof(unsigned long long)) != cudaSuccess ||
+            cudaMallocHost(&o->count_host, sizeof(unsigned long long)) != cudaSuccess) {
+            cudaGetLastError();
+            return GS_ERR_OOM;
+        }
+    }
+    // Pinned gradients are read in place by the step kernel over the CPU-GPU
+    // link, so only the visible rows' gradients cross it; other host memory
+    // is copied to device staging first.
+    if (n) {
+        const float *mx = mapped_host(gh->xyz, 4), *ms = mapped_host(gh->scale, 4), *mr = mapped_host(gh->rot, 16),
+                    *mo = mapped_host(gh->opacity, 4), *mh = mapped_host(gh->sh, 16);
+        if (mx && ms && mr && mo && mh) {
+            gs_grads gd{mx, ms, mr, mo, mh};
+            StepArgs a;
+            fill_args(o, params, &a);
+            set_attrs(&a, attrs, &gd);
+            memcpy(a.cam, cam, sizeof(a.cam));
+            a.n_visible = o->count;
+            a.g_host = 1;
+            cudaError_t e = cudaMemsetAsync(o->count, 0, sizeof(unsigned long long), s);
+            if (e == cudaSuccess) e = gs::launch_step(a, o->cfg.prec, gs::kVisCamera, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(o->count_host, o->count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return fail_cuda(o, e);
+            *n_visible_host = (int64_t)*o->count_host;
+            return GS_OK;
+        }
+    }
     // staging: five groups at 256-B aligned offsets
     const int64_t w[5] = {3, 3, 4, 1, 48};
     int64_t off[5], tot = 0;

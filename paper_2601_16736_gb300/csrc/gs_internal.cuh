@@ -89,6 +89,7 @@ struct StepArgs {
     float tau_act;               // active iff tau > tau_act (largest float below -ln 254)
     uint64_t aiu_thr;            // AIU-sampled iff (draw >> 11) < aiu_thr
     unsigned long long *n_active;   // optional, accumulated with atomicAdd
+    int32_t g_host;              // gradients are pinned host memory read in place
 };
 
 // ------------------------------------------------------- device helpers

@@ -500,7 +500,7 @@ __device__ __forceinline__ void prefetch_row_l2(const StepArgs &a, int32_t row)
 {
     const size_t r = (size_t)row;
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], 192;" ::"l"(a.a_sh + r * 48) : "memory");
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], 192;" ::"l"(a.g_sh + r * 48) : "memory");
+    if (!a.g_host) asm volatile("cp.async.bulk.prefetch.L2.global [%0], 192;" ::"l"(a.g_sh + r * 48) : "memory");
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(static_cast<const char *>(a.m) + r * kRowBytes),
                  "n"(kRowBytes) : "memory");
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(static_cast<const char *>(a.v) + r * kRowBytes),
