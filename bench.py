@@ -538,7 +538,7 @@ def reindex_leg(G, synth, steps, prec="bf16_hybrid", n_events=3):
     return res
 
 
-def batched_leg(G, synth, steps, n_scenes=16, seed=1004):
+def batched_leg(G, synth, steps, n_scenes=16, seed=1004, prec="fp32"):
     """16 independent scenes, primitive counts log-uniform in [50k, 2M] and
     blob extents log-uniform in [6, 75] (10-60 % visible), each with its own
     camera sequence and step counters: 16 separate FP32 launches per step vs
@@ -574,9 +574,9 @@ def batched_leg(G, synth, steps, n_scenes=16, seed=1004):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / 1e3, int(counts.sum().item())
 
-    res = {"workload": f"{n_scenes} scenes, {total} Gaussians in total (sizes log-uniform 50k-2M), FP32 moments",
+    res = {"workload": f"{n_scenes} scenes, {total} Gaussians in total (sizes log-uniform 50k-2M)",
            "sizes": sizes.tolist()}
-    # 16 separate launches per step
+    # 16 separate FP32 launches per step
     hs = [G.gs_opt_init(G.make_config(), sc["n"]) for sc in scenes]
 
     def sep(k, counts):
@@ -602,6 +602,18 @@ def batched_leg(G, synth, steps, n_scenes=16, seed=1004):
     res["batched_graph"] = {"value": nv / dt, "ms_per_step": dt / steps * 1e3, "launches_per_step": 1}
     res["speedup_batched_vs_separate"] = res["batched_persistent"]["value"] / res["separate_launches"]["value"]
     res["speedup_graph_vs_separate"] = res["batched_graph"]["value"] / res["separate_launches"]["value"]
+    b.close()
+    for h in hs:
+        G.gs_opt_destroy(h)
+    # the same batch with FP16-block moments (passes the 1e-3 gate), graph replay
+    hs = [G.gs_opt_init(G.make_config(prec=PREC_ENUM["fp16_block"]), sc["n"]) for sc in scenes]
+    b = G.gs_batch_create(hs)
+    timed(bat, 2 * 3 + 4, 5000)
+    timed(lambda k, c: bat(k, c, True), 3, 6000)
+    dt, nv = timed(lambda k, c: bat(k, c, True), steps, 7000)
+    res["batched_graph_fp16_block"] = {"value": nv / dt, "ms_per_step": dt / steps * 1e3, "launches_per_step": 1,
+                                       "tuned": G.gs_batch_config(b),
+                                       "speedup_vs_separate_fp32": (nv / dt) / res["separate_launches"]["value"]}
     b.close()
     for h in hs:
         G.gs_opt_destroy(h)

@@ -87,8 +87,8 @@ typedef enum gs_moment_prec {
                                the same hash).  128 B per moment and row, as BF16.
                                The step count t saturates at 65535 (the
                                bias-correction factors are exactly 1 from step
-                               15936 on).  Not available with position noise, AIU,
-                               the active count or gs_batch_*.                    */
+                               15936 on).  Not available with position noise, AIU
+                               or the active count.                               */
 } gs_moment_prec;
 
 /* Regulariser form.  GS_REG_DAR is the paper's AdamW-GS (Eq. disentangled_adam);

@@ -279,12 +279,18 @@ const BatchCandidate kCandHyb[] = {
     {256, 4, 4, launch_batch_t<256, 4, GS_MOM_BF16_HYBRID, 4>},
 };
 
+const BatchCandidate kCandF16B[] = {
+    {256, 8, 4, launch_batch_t<256, 4, GS_MOM_FP16_BLOCK, 8>},
+    {512, 8, 4, launch_batch_t<512, 4, GS_MOM_FP16_BLOCK, 8>},
+};
+
 const BatchCandidate *candidates(int prec, int *n)
 {
     switch (prec) {
     case GS_MOM_FP32: *n = 4; return kCandF32;
     case GS_MOM_BF16: *n = 3; return kCandBf16;
     case GS_MOM_BF16_HYBRID: *n = 3; return kCandHyb;
+    case GS_MOM_FP16_BLOCK: *n = 2; return kCandF16B;
     default: *n = 0; return nullptr;
     }
 }

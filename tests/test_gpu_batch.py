@@ -41,12 +41,12 @@ def _scenes(prec_name, G):
     return runs_b, runs_s, cams
 
 
-@pytest.mark.parametrize("prec", ["FP32", "BF16_HYBRID"])
+@pytest.mark.parametrize("prec", ["FP32", "BF16_HYBRID", "FP16_BLOCK"])
 def test_batch_equals_single_scene_steps(G, prec):
     runs_b, runs_s, cams = _scenes(prec, G)
     b = G.gs_batch_create([r.h for r in runs_b])
     nvis = torch.zeros(len(SIZES), dtype=torch.int64, device="cuda")
-    n_cand = {"FP32": 4, "BF16_HYBRID": 3}[prec]
+    n_cand = {"FP32": 4, "BF16_HYBRID": 3, "FP16_BLOCK": 2}[prec]
     steps = 3 * n_cand + 6                  # tuning, then the tuned eager and graph paths
     for k in range(1, steps + 1):
         for s, (rb, rs) in enumerate(zip(runs_b, runs_s)):

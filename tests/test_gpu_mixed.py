@@ -207,10 +207,9 @@ def test_3m_1000_steps_sampled(G, orc, prec, gate):
         assert e <= gate, f"{prec} group {g}: {e:.2e} > {gate:.0e}"
 
 
-def test_fp16_block_rejects_optional_terms_and_batches(G):
-    """FP16-block moments have no extended-step or batched variant: those
-    requests are refused before anything is launched, and the context stays
-    usable."""
+def test_fp16_block_rejects_optional_terms(G):
+    """FP16-block moments have no extended-step variant: those requests are
+    refused before anything is launched, and the context stays usable."""
     n = 1000
     run = GpuRun(synth.scene_uniform(n, 930), prec=G.GS_MOM_FP16_BLOCK)
     mask = torch.ones(n, dtype=torch.uint8, device="cuda")
@@ -219,9 +218,6 @@ def test_fp16_block_rejects_optional_terms_and_batches(G):
         with pytest.raises(G.GsError) as e:
             run.step_mask(mask, G.make_params(LR, 1, **kw))
         assert e.value.status == G.GS_ERR_UNSUPPORTED
-    with pytest.raises(G.GsError) as e:
-        G.gs_batch_create([run.h])
-    assert e.value.status == G.GS_ERR_UNSUPPORTED
     run.step_mask(mask, G.make_params(LR, 1))         # the plain step still runs
     torch.cuda.synchronize()
     assert G.gs_opt_sync_errors(run.h) == G.GS_OK
