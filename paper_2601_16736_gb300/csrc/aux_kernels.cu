@@ -244,39 +244,44 @@ __global__ void import_f16b_kernel(const StateView st, int32_t n, const float *_
 
 // ----------------------------------------------------------- attribute gather
 // One thread per (output row, canonical column).
-// 16 lanes per output row: lanes 0-11 move the 12 float4 of the SH row,
-// lane 12 the rotation float4, lanes 13-15 xyz, scale and opacity.  Nothing
-// is read again, so loads and stores stream past L2.
-constexpr int kGatherLanes = 16;
+// A flat index space: first one thread per float4 of the 16-B aligned groups
+// (12 SH float4 and the rotation of each row), then one thread per row for
+// its seven small values (xyz, scale, opacity).  Consecutive threads write
+// consecutive output addresses, and read consecutive input addresses wherever
+// the sources run in order (a prune keeps them so).  Nothing is read again,
+// so loads and stores stream past L2.
+constexpr int kGatherVec = 13;
 
 __global__ void gather_attrs_kernel(const gs_attrs in, int32_t n_in, const gs_attrs out,
                                     const int32_t *__restrict__ src, int32_t n_new, int32_t *err)
 {
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t j = gid / kGatherLanes;
-    const int c = (int)(gid % kGatherLanes);
-    if (j >= n_new) return;
-    const int32_t s = src[j];
-    if (s < 0) return;
-    if (s >= n_in) {
-        if (c == 0) record_error(err, GS_ERR_INVALID_ARG);
-        return;
-    }
-    if (c < 12) {
-        const float4 x = __ldcs(reinterpret_cast<const float4 *>(in.sh) + (int64_t)s * 12 + c);
-        __stcs(reinterpret_cast<float4 *>(out.sh) + j * 12 + c, x);
-    } else if (c == 12) {
-        __stcs(reinterpret_cast<float4 *>(out.rot) + j, __ldcs(reinterpret_cast<const float4 *>(in.rot) + s));
-    } else if (c == 15) {
-        __stcs(out.opacity + j, __ldcs(in.opacity + s));
-    } else {
-        const float *ip = c == 13 ? in.xyz : in.scale;
-        float *op = c == 13 ? out.xyz : out.scale;
-        const float a = __ldcs(ip + (int64_t)s * 3), b = __ldcs(ip + (int64_t)s * 3 + 1),
-                    d = __ldcs(ip + (int64_t)s * 3 + 2);
-        __stcs(op + j * 3, a);
-        __stcs(op + j * 3 + 1, b);
-        __stcs(op + j * 3 + 2, d);
+    const int64_t n = n_new;
+    if (gid < kGatherVec * n) {
+        const int64_t j = gid / kGatherVec;
+        const int k = (int)(gid - kGatherVec * j);
+        const int32_t s = src[j];
+        if (s < 0) return;
+        if (s >= n_in) {
+            if (k == 0) record_error(err, GS_ERR_INVALID_ARG);
+            return;
+        }
+        if (k < 12)
+            __stcs(reinterpret_cast<float4 *>(out.sh) + j * 12 + k,
+                   __ldcs(reinterpret_cast<const float4 *>(in.sh) + (int64_t)s * 12 + k));
+        else
+            __stcs(reinterpret_cast<float4 *>(out.rot) + j, __ldcs(reinterpret_cast<const float4 *>(in.rot) + s));
+    } else if (gid < (kGatherVec + 1) * n) {
+        const int64_t j = gid - kGatherVec * n;
+        const int32_t s = src[j];
+        if (s < 0 || s >= n_in) return;            // an out-of-range source is recorded above
+        const int64_t r = s;
+        const float x0 = __ldcs(in.xyz + r * 3), x1 = __ldcs(in.xyz + r * 3 + 1), x2 = __ldcs(in.xyz + r * 3 + 2);
+        const float s0 = __ldcs(in.scale + r * 3), s1 = __ldcs(in.scale + r * 3 + 1), s2 = __ldcs(in.scale + r * 3 + 2);
+        const float op = __ldcs(in.opacity + r);
+        __stcs(out.xyz + j * 3, x0); __stcs(out.xyz + j * 3 + 1, x1); __stcs(out.xyz + j * 3 + 2, x2);
+        __stcs(out.scale + j * 3, s0); __stcs(out.scale + j * 3 + 1, s1); __stcs(out.scale + j * 3 + 2, s2);
+        __stcs(out.opacity + j, op);
     }
 }
 
@@ -389,8 +394,8 @@ cudaError_t launch_reindex(const StateView &in, int32_t n_in, const StateView &o
 {
     if (n_out <= 0) return cudaSuccess;
     switch (in.prec) {
-    case GS_MOM_FP32:
-        reindex_kernel<15, kRowBytesF32><<<blocks_for((int64_t)n_out * 15), kThreads, 0, s>>>(in, n_in, out, n_out,
+    case GS_MOM_FP32:      // whole 256-B rows (the last 16 B are padding): a warp moves two rows
+        reindex_kernel<16, kRowBytesF32><<<blocks_for((int64_t)n_out * 16), kThreads, 0, s>>>(in, n_in, out, n_out,
                                                                                              src, reset, err);
         break;
     case GS_MOM_BF16:
@@ -437,7 +442,7 @@ cudaError_t launch_gather_attrs(const gs_attrs &in, int32_t n_in, const gs_attrs
                                 int32_t n_new, int32_t *err, cudaStream_t s)
 {
     if (n_new <= 0) return cudaSuccess;
-    gather_attrs_kernel<<<blocks_for((int64_t)n_new * kGatherLanes), kThreads, 0, s>>>(in, n_in, out, src, n_new, err);
+    gather_attrs_kernel<<<blocks_for((int64_t)n_new * (kGatherVec + 1)), kThreads, 0, s>>>(in, n_in, out, src, n_new, err);
     return cudaGetLastError();
 }
 
