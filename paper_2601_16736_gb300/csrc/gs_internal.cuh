@@ -177,8 +177,9 @@ __device__ __forceinline__ float step_element(float th, float g, float &m, float
 // the largest magnitude in [2^14, 2^15).
 __device__ __forceinline__ uint32_t group_exponent(const float *x, int n)
 {
-    uint32_t e = 0;
-    for (int q = 0; q < n; ++q) e = max(e, (__float_as_uint(x[q]) >> 23) & 0xffu);
+    uint32_t b = 0;                       // the largest magnitude's bits
+    for (int q = 0; q < n; ++q) b = max(b, __float_as_uint(x[q]) & 0x7fffffffu);
+    const uint32_t e = b >> 23;
     return e < 15u ? 0u : e;
 }
 // 2^(141 - e) and 2^(e - 141) as exact FP32 powers of two (15 <= e <= 254)

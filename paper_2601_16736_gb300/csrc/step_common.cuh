@@ -285,29 +285,43 @@ struct State<GS_MOM_BF16_HYBRID> {
 // every value within 2^29 of it is an FP16 normal with a 10-bit mantissa.
 // e < 15 (all magnitudes below 2^-112) stores zeros and e = 0.
 
-// FP32 -> FP16 bits rounded stochastically: 13 random bits added below the
-// 10 mantissa bits FP16 keeps, then truncated (exact in FP16 for normals).
-// FP16 subnormals (more than 2^29 below the group's maximum) round to nearest.
-__device__ __forceinline__ uint32_t h_bits_sr(float y, uint32_t rnd13)
+// Packed FP16 words: value 2k in the low half of word k, value 2k+1 in the high half.
+
+// Two values scaled by s, to nearest.
+__device__ __forceinline__ uint32_t h2_rn(float x, float y)
 {
-    const uint32_t u = __float_as_uint(y);
-    if ((u & 0x7f800000u) < (113u << 23) || (u & 0x7f800000u) == 0x7f800000u) return h_bits(y);
-    return h_bits(__uint_as_float((u + (rnd13 & 0x1fffu)) & ~0x1fffu));
+    const __half2 h = __floats2half2_rn(x, y);
+    return *reinterpret_cast<const uint32_t *>(&h);
 }
 
-// n values -> FP16 bits (into h) and the group exponent; m to nearest, v
-// stochastically from hashes of (seed, iteration, row, first column).
+// Two values rounded stochastically: random bits (13 each) added below the
+// 10 mantissa bits FP16 keeps, then truncated by one conversion.  Exact
+// stochastic rounding for FP16 normals (values within 2^29 of the group's
+// largest); Inf and NaN pass unchanged.
+__device__ __forceinline__ uint32_t h2_sr(float x, float y, uint32_t rnd)
+{
+    uint32_t ux = __float_as_uint(x), uy = __float_as_uint(y);
+    ux += (ux & 0x7f800000u) != 0x7f800000u ? (rnd & 0x1fffu) : 0u;
+    uy += (uy & 0x7f800000u) != 0x7f800000u ? ((rnd >> 16) & 0x1fffu) : 0u;
+    uint32_t d;
+    asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(__uint_as_float(uy)), "f"(__uint_as_float(ux)));
+    return d;
+}
+
+// n values -> (n + 1) / 2 packed words and the group exponent; m to nearest,
+// v stochastically from hashes of (seed, iteration, row, first column).  An
+// odd n leaves the last word's high half zero.
 template <int n>
-__device__ __forceinline__ uint32_t encode_rn(const float *x, uint32_t *h)
+__device__ __forceinline__ uint32_t encode_rn_w(const float *x, uint32_t *w)
 {
     const uint32_t e = group_exponent(x, n);
     const float s = e ? enc_scale(e) : 0.f;
 #pragma unroll
-    for (int q = 0; q < n; ++q) h[q] = e ? h_bits(x[q] * s) : 0u;
+    for (int q = 0; q < n; q += 2) w[q / 2] = h2_rn(x[q] * s, q + 1 < n ? x[q + 1] * s : 0.f);
     return e;
 }
 template <int n>
-__device__ __forceinline__ uint32_t encode_sr(const float *x, uint32_t *h, const StepArgs &a, int32_t r, int col0)
+__device__ __forceinline__ uint32_t encode_sr_w(const float *x, uint32_t *w, const StepArgs &a, int32_t r, int col0)
 {
     const uint32_t e = group_exponent(x, n);
     const float s = e ? enc_scale(e) : 0.f;
@@ -315,14 +329,20 @@ __device__ __forceinline__ uint32_t encode_sr(const float *x, uint32_t *h, const
     for (int q = 0; q < n; q += 2) {
         const uint32_t rnd = fmix32((uint32_t)r * 0x9e3779b1u ^ (uint32_t)(col0 + q) * 0x85ebca77u ^
                                     (uint32_t)a.k_ctr * 0xc2b2ae3du ^ (uint32_t)a.seed ^ 0x165667b1u);
-        h[q] = e ? h_bits_sr(x[q] * s, rnd) : 0u;
-        if (q + 1 < n) h[q + 1] = e ? h_bits_sr(x[q + 1] * s, rnd >> 16) : 0u;
+        w[q / 2] = h2_sr(x[q] * s, q + 1 < n ? x[q + 1] * s : 0.f, rnd);
     }
     return e;
 }
-__device__ __forceinline__ float h_val(uint32_t bits16, float d)
+// n values from packed words, times the group's decode scale d.
+template <int n>
+__device__ __forceinline__ void decode_w(const uint32_t *w, float d, float *x)
 {
-    return __half2float(__ushort_as_half((unsigned short)(bits16 & 0xffffu))) * d;
+#pragma unroll
+    for (int q = 0; q < n; q += 2) {
+        const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w[q / 2]));
+        x[q] = f.x * d;
+        if (q + 1 < n) x[q + 1] = f.y * d;
+    }
 }
 
 template <>
@@ -339,27 +359,19 @@ struct State<GS_MOM_FP16_BLOCK> {
         static_assert(kW == 8, "FP16 block items cover 8 SH columns");
         const char *mr = row(a.m, r), *vr = row(a.v, r);
         const uint4 um = *reinterpret_cast<const uint4 *>(mr + 16 * i), uv = *reinterpret_cast<const uint4 *>(vr + 16 * i);
-        const float dm = dec_scale((uint8_t)mr[kF16BExp + i]), dv = dec_scale((uint8_t)vr[kF16BExp + i]);
         const uint32_t wm[4] = {um.x, um.y, um.z, um.w}, wv[4] = {uv.x, uv.y, uv.z, uv.w};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            m[2 * q] = h_val(wm[q], dm);
-            m[2 * q + 1] = h_val(wm[q] >> 16, dm);
-            v[2 * q] = h_val(wv[q], dv);
-            v[2 * q + 1] = h_val(wv[q] >> 16, dv);
-        }
+        decode_w<8>(wm, dec_scale((uint8_t)mr[kF16BExp + i]), m);
+        decode_w<8>(wv, dec_scale((uint8_t)vr[kF16BExp + i]), v);
     }
     template <int kW>
     static __device__ __forceinline__ void store_sh(const StepArgs &a, int32_t r, int i, const float *m,
                                                     const float *v, uint32_t)
     {
         char *mr = row(a.m, r), *vr = row(a.v, r);
-        uint32_t hm[8], hv[8];
-        const uint32_t em = encode_rn<8>(m, hm), ev = encode_sr<8>(v, hv, a, r, 11 + 8 * i);
-        __stcs(reinterpret_cast<uint4 *>(mr + 16 * i), make_uint4(hm[0] | hm[1] << 16, hm[2] | hm[3] << 16,
-                                                                  hm[4] | hm[5] << 16, hm[6] | hm[7] << 16));
-        __stcs(reinterpret_cast<uint4 *>(vr + 16 * i), make_uint4(hv[0] | hv[1] << 16, hv[2] | hv[3] << 16,
-                                                                  hv[4] | hv[5] << 16, hv[6] | hv[7] << 16));
+        uint32_t wm[4], wv[4];
+        const uint32_t em = encode_rn_w<8>(m, wm), ev = encode_sr_w<8>(v, wv, a, r, 11 + 8 * i);
+        __stcs(reinterpret_cast<uint4 *>(mr + 16 * i), make_uint4(wm[0], wm[1], wm[2], wm[3]));
+        __stcs(reinterpret_cast<uint4 *>(vr + 16 * i), make_uint4(wv[0], wv[1], wv[2], wv[3]));
         mr[kF16BExp + i] = (char)em;
         vr[kF16BExp + i] = (char)ev;
     }
@@ -367,8 +379,9 @@ struct State<GS_MOM_FP16_BLOCK> {
 
 // The small columns of an FP16-block row in two items: c = 12 rotation (4
 // values at kF16BRot, exponent 6), c = 13 xyz + scale + opacity (7 values at
-// kF16BXso, exponent 7) with the step count t (uint16, saturating) beside
-// them.  The visible update as small_item; RSR scales the moments afterwards.
+// kF16BXso, exponent 7) with the step count t (uint16, saturating) in the
+// high half of the fourth word.  The visible update as small_item; RSR
+// scales the moments afterwards.
 __device__ __forceinline__ void small_item_f16b(const StepArgs &a, const int32_t row, const int c, const bool sampled,
                                                 const float2 f)
 {
@@ -377,9 +390,10 @@ __device__ __forceinline__ void small_item_f16b(const StepArgs &a, const int32_t
     const size_t r = (size_t)row;
     if (c == 12) {
         const uint2 um = *reinterpret_cast<const uint2 *>(mr + kF16BRot), uv = *reinterpret_cast<const uint2 *>(vr + kF16BRot);
-        const float dm = dec_scale((uint8_t)mr[kF16BExp + 6]), dv = dec_scale((uint8_t)vr[kF16BExp + 6]);
-        float m[4] = {h_val(um.x, dm), h_val(um.x >> 16, dm), h_val(um.y, dm), h_val(um.y >> 16, dm)};
-        float v[4] = {h_val(uv.x, dv), h_val(uv.x >> 16, dv), h_val(uv.y, dv), h_val(uv.y >> 16, dv)};
+        const uint32_t wm[2] = {um.x, um.y}, wv[2] = {uv.x, uv.y};
+        float m[4], v[4];
+        decode_w<4>(wm, dec_scale((uint8_t)mr[kF16BExp + 6]), m);
+        decode_w<4>(wv, dec_scale((uint8_t)vr[kF16BExp + 6]), v);
         float *pt = a.a_rot + r * 4;
         float4 th = ld4(pt);
         const float4 g = ldg4_stream(a.g_rot + r * 4);
@@ -396,22 +410,18 @@ __device__ __forceinline__ void small_item_f16b(const StepArgs &a, const int32_t
                 v[q] *= a.alpha2;
             }
         }
-        uint32_t hm[4], hv[4];
-        const uint32_t em = encode_rn<4>(m, hm), ev = encode_sr<4>(v, hv, a, row, 6);
-        __stcs(reinterpret_cast<uint2 *>(mr + kF16BRot), make_uint2(hm[0] | hm[1] << 16, hm[2] | hm[3] << 16));
-        __stcs(reinterpret_cast<uint2 *>(vr + kF16BRot), make_uint2(hv[0] | hv[1] << 16, hv[2] | hv[3] << 16));
+        uint32_t hm[2], hv[2];
+        const uint32_t em = encode_rn_w<4>(m, hm), ev = encode_sr_w<4>(v, hv, a, row, 6);
+        __stcs(reinterpret_cast<uint2 *>(mr + kF16BRot), make_uint2(hm[0], hm[1]));
+        __stcs(reinterpret_cast<uint2 *>(vr + kF16BRot), make_uint2(hv[0], hv[1]));
         mr[kF16BExp + 6] = (char)em;
         vr[kF16BExp + 6] = (char)ev;
     } else {
         const uint4 um = *reinterpret_cast<const uint4 *>(mr + kF16BXso), uv = *reinterpret_cast<const uint4 *>(vr + kF16BXso);
-        const float dm = dec_scale((uint8_t)mr[kF16BExp + 7]), dv = dec_scale((uint8_t)vr[kF16BExp + 7]);
-        const uint32_t wm[4] = {um.x, um.y, um.z, um.w}, wv[4] = {uv.x, uv.y, uv.z, uv.w};
+        const uint32_t wm[4] = {um.x, um.y, um.z, um.w & 0xffffu}, wv[4] = {uv.x, uv.y, uv.z, uv.w};
         float m[7], v[7];
-#pragma unroll
-        for (int q = 0; q < 7; ++q) {
-            m[q] = h_val(wm[q / 2] >> (16 * (q & 1)), dm);
-            v[q] = h_val(wv[q / 2] >> (16 * (q & 1)), dv);
-        }
+        decode_w<7>(wm, dec_scale((uint8_t)mr[kF16BExp + 7]), m);
+        decode_w<7>(wv, dec_scale((uint8_t)vr[kF16BExp + 7]), v);
         uint32_t t = um.w >> 16;
         float *px = a.a_xyz + r * 3, *ps = a.a_scale + r * 3, *po = a.a_op + r;
         float x0 = px[0], x1 = px[1], x2 = px[2], s0 = ps[0], s1 = ps[1], s2 = ps[2], op = *po;
@@ -440,12 +450,10 @@ __device__ __forceinline__ void small_item_f16b(const StepArgs &a, const int32_t
                 v[q] *= a.alpha2;
             }
         }
-        uint32_t hm[7], hv[7];
-        const uint32_t em = encode_rn<7>(m, hm), ev = encode_sr<7>(v, hv, a, row, 0);
-        __stcs(reinterpret_cast<uint4 *>(mr + kF16BXso), make_uint4(hm[0] | hm[1] << 16, hm[2] | hm[3] << 16,
-                                                                   hm[4] | hm[5] << 16, hm[6] | t << 16));
-        __stcs(reinterpret_cast<uint4 *>(vr + kF16BXso), make_uint4(hv[0] | hv[1] << 16, hv[2] | hv[3] << 16,
-                                                                   hv[4] | hv[5] << 16, hv[6]));
+        uint32_t hm[4], hv[4];
+        const uint32_t em = encode_rn_w<7>(m, hm), ev = encode_sr_w<7>(v, hv, a, row, 0);
+        __stcs(reinterpret_cast<uint4 *>(mr + kF16BXso), make_uint4(hm[0], hm[1], hm[2], hm[3] | t << 16));
+        __stcs(reinterpret_cast<uint4 *>(vr + kF16BXso), make_uint4(hv[0], hv[1], hv[2], hv[3]));
         mr[kF16BExp + 7] = (char)em;
         vr[kF16BExp + 7] = (char)ev;
     }
@@ -458,32 +466,27 @@ __device__ __forceinline__ void rsr_small_f16b(const StepArgs &a, const int32_t 
     char *mr = S::row(a.m, row), *vr = S::row(a.v, row);
     if (c == 12) {
         const uint2 um = *reinterpret_cast<const uint2 *>(mr + kF16BRot), uv = *reinterpret_cast<const uint2 *>(vr + kF16BRot);
-        const float dm = dec_scale((uint8_t)mr[kF16BExp + 6]) * a.alpha1, dv = dec_scale((uint8_t)vr[kF16BExp + 6]) * a.alpha2;
-        float m[4] = {h_val(um.x, dm), h_val(um.x >> 16, dm), h_val(um.y, dm), h_val(um.y >> 16, dm)};
-        float v[4] = {h_val(uv.x, dv), h_val(uv.x >> 16, dv), h_val(uv.y, dv), h_val(uv.y >> 16, dv)};
-        uint32_t hm[4], hv[4];
-        const uint32_t em = encode_rn<4>(m, hm), ev = encode_sr<4>(v, hv, a, row, 6);
-        __stcs(reinterpret_cast<uint2 *>(mr + kF16BRot), make_uint2(hm[0] | hm[1] << 16, hm[2] | hm[3] << 16));
-        __stcs(reinterpret_cast<uint2 *>(vr + kF16BRot), make_uint2(hv[0] | hv[1] << 16, hv[2] | hv[3] << 16));
+        const uint32_t wm[2] = {um.x, um.y}, wv[2] = {uv.x, uv.y};
+        float m[4], v[4];
+        decode_w<4>(wm, dec_scale((uint8_t)mr[kF16BExp + 6]) * a.alpha1, m);
+        decode_w<4>(wv, dec_scale((uint8_t)vr[kF16BExp + 6]) * a.alpha2, v);
+        uint32_t hm[2], hv[2];
+        const uint32_t em = encode_rn_w<4>(m, hm), ev = encode_sr_w<4>(v, hv, a, row, 6);
+        __stcs(reinterpret_cast<uint2 *>(mr + kF16BRot), make_uint2(hm[0], hm[1]));
+        __stcs(reinterpret_cast<uint2 *>(vr + kF16BRot), make_uint2(hv[0], hv[1]));
         mr[kF16BExp + 6] = (char)em;
         vr[kF16BExp + 6] = (char)ev;
     } else {
         const uint4 um = *reinterpret_cast<const uint4 *>(mr + kF16BXso), uv = *reinterpret_cast<const uint4 *>(vr + kF16BXso);
-        const float dm = dec_scale((uint8_t)mr[kF16BExp + 7]) * a.alpha1, dv = dec_scale((uint8_t)vr[kF16BExp + 7]) * a.alpha2;
-        const uint32_t wm[4] = {um.x, um.y, um.z, um.w}, wv[4] = {uv.x, uv.y, uv.z, uv.w};
+        const uint32_t wm[4] = {um.x, um.y, um.z, um.w & 0xffffu}, wv[4] = {uv.x, uv.y, uv.z, uv.w};
         float m[7], v[7];
-#pragma unroll
-        for (int q = 0; q < 7; ++q) {
-            m[q] = h_val(wm[q / 2] >> (16 * (q & 1)), dm);
-            v[q] = h_val(wv[q / 2] >> (16 * (q & 1)), dv);
-        }
+        decode_w<7>(wm, dec_scale((uint8_t)mr[kF16BExp + 7]) * a.alpha1, m);
+        decode_w<7>(wv, dec_scale((uint8_t)vr[kF16BExp + 7]) * a.alpha2, v);
         const uint32_t t = um.w >> 16;
-        uint32_t hm[7], hv[7];
-        const uint32_t em = encode_rn<7>(m, hm), ev = encode_sr<7>(v, hv, a, row, 0);
-        __stcs(reinterpret_cast<uint4 *>(mr + kF16BXso), make_uint4(hm[0] | hm[1] << 16, hm[2] | hm[3] << 16,
-                                                                   hm[4] | hm[5] << 16, hm[6] | t << 16));
-        __stcs(reinterpret_cast<uint4 *>(vr + kF16BXso), make_uint4(hv[0] | hv[1] << 16, hv[2] | hv[3] << 16,
-                                                                   hv[4] | hv[5] << 16, hv[6]));
+        uint32_t hm[4], hv[4];
+        const uint32_t em = encode_rn_w<7>(m, hm), ev = encode_sr_w<7>(v, hv, a, row, 0);
+        __stcs(reinterpret_cast<uint4 *>(mr + kF16BXso), make_uint4(hm[0], hm[1], hm[2], hm[3] | t << 16));
+        __stcs(reinterpret_cast<uint4 *>(vr + kF16BXso), make_uint4(hv[0], hv[1], hv[2], hv[3]));
         mr[kF16BExp + 7] = (char)em;
         vr[kF16BExp + 7] = (char)ev;
     }

@@ -117,19 +117,13 @@ __device__ __forceinline__ void tile_decide(const StepArgs &a, const int vis_src
 
 // ---------------------------------------------------------------- the kernel
 
-// One tile: phase A, then the items of its visible and invisible-sampled rows.
+// Phase B of one tile: the items of its visible and invisible-sampled rows
+// (nv, nr of them in L), grouped by kind: all SH items, then the small
+// items, then RSR.
 template <int kTile, int kPrec, int kW>
-__device__ __forceinline__ void process_tile(const StepArgs &a, const int vis_src, const int64_t r0,
-                                             TileLists<kTile> &L)
+__device__ __forceinline__ void tile_items(const StepArgs &a, const TileLists<kTile> &L, const int nv, const int nr)
 {
-    static_assert(kTile % kThreads == 0, "tile must be a multiple of the block");
-    static_assert(kW == 4 || kW == 8, "SH items cover 4 or 8 columns");
-    using S = State<kPrec>;
     constexpr int kNsh = 48 / kW, kItems = kNsh + kSmallItems<kPrec>;
-    int nv, nr;
-    tile_decide<kTile, S::kRowBytes, S::kTByte>(a, vis_src, r0, L, nv, nr);
-
-    // items grouped by kind: all SH items, then the small items, then RSR
     const int e_sh = kNsh * nv, e_vis = kItems * nv, e_all = e_vis + kItems * nr;
     for (int w = threadIdx.x; w < e_all; w += kThreads) {
         if (w < e_sh) {
@@ -147,6 +141,19 @@ __device__ __forceinline__ void process_tile(const StepArgs &a, const int vis_sr
             rsr_item<kPrec, kW>(a, L.rlist[j], i);
         }
     }
+}
+
+// One tile: phase A, then its items.
+template <int kTile, int kPrec, int kW>
+__device__ __forceinline__ void process_tile(const StepArgs &a, const int vis_src, const int64_t r0,
+                                             TileLists<kTile> &L)
+{
+    static_assert(kTile % kThreads == 0, "tile must be a multiple of the block");
+    static_assert(kW == 4 || kW == 8, "SH items cover 4 or 8 columns");
+    using S = State<kPrec>;
+    int nv, nr;
+    tile_decide<kTile, S::kRowBytes, S::kTByte>(a, vis_src, r0, L, nv, nr);
+    tile_items<kTile, kPrec, kW>(a, L, nv, nr);
 }
 
 template <int kTile, int kMinBlocks, int kPrec, int kW>
@@ -206,28 +213,29 @@ constexpr int kStepTile = 256;
 constexpr int kStepMinBlocks = 4;      // 64 registers: 4 CTAs of 256 threads per SM
 constexpr int kShWF32 = 4, kShWBf16 = 8;   // SH columns per item
 
+namespace {
+
+template <int kPrec, int kW>
+cudaError_t launch_tiles(const StepArgs &a, int vis_src, cudaStream_t s)
+{
+    const unsigned n_tiles = (unsigned)((a.n_rows + kStepTile - 1) / kStepTile);
+    step_tile<kStepTile, kStepMinBlocks, kPrec, kW><<<n_tiles, kThreads, 0, s>>>(a, vis_src);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
 cudaError_t launch_step(const StepArgs &a, int prec, int vis_src, cudaStream_t s)
 {
     if (a.n_rows <= 0) return cudaSuccess;
     if (a.noise || a.aiu || a.n_active) return launch_step_ext(a, prec, vis_src, s);
-    const unsigned grid = (unsigned)((a.n_rows + kStepTile - 1) / kStepTile);
     switch (prec) {
-    case GS_MOM_FP32:
-        step_tile<kStepTile, kStepMinBlocks, GS_MOM_FP32, kShWF32><<<grid, kThreads, 0, s>>>(a, vis_src);
-        break;
-    case GS_MOM_BF16:
-        step_tile<kStepTile, kStepMinBlocks, GS_MOM_BF16, kShWBf16><<<grid, kThreads, 0, s>>>(a, vis_src);
-        break;
-    case GS_MOM_BF16_HYBRID:
-        step_tile<kStepTile, kStepMinBlocks, GS_MOM_BF16_HYBRID, kShWBf16><<<grid, kThreads, 0, s>>>(a, vis_src);
-        break;
-    case GS_MOM_FP16_BLOCK:
-        step_tile<kStepTile, kStepMinBlocks, GS_MOM_FP16_BLOCK, 8><<<grid, kThreads, 0, s>>>(a, vis_src);
-        break;
-    default:
-        return cudaErrorNotSupported;
+    case GS_MOM_FP32: return launch_tiles<GS_MOM_FP32, kShWF32>(a, vis_src, s);
+    case GS_MOM_BF16: return launch_tiles<GS_MOM_BF16, kShWBf16>(a, vis_src, s);
+    case GS_MOM_BF16_HYBRID: return launch_tiles<GS_MOM_BF16_HYBRID, kShWBf16>(a, vis_src, s);
+    case GS_MOM_FP16_BLOCK: return launch_tiles<GS_MOM_FP16_BLOCK, 8>(a, vis_src, s);
+    default: return cudaErrorNotSupported;
     }
-    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------ batched launch
