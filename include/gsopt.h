@@ -83,15 +83,14 @@ typedef enum gs_moment_prec {
                                rotation; xyz + scale + opacity): the group's largest
                                magnitude is scaled into FP16's top binade, so every
                                value within 2^29 of it keeps FP16's 10-bit mantissa.
-                               m rounded to nearest, v stochastically (13 random
-                               bits from the same hash below the kept mantissa;
-                               values further than 2^29 below their group's
-                               largest are all but truncated).  128 B per moment
-                               and row, as BF16.
+                               m rounded to nearest, v stochastically (dithered by
+                               +-1/2 FP16 ulp from the same hash, then rounded to
+                               nearest; values further than 2^29 below their
+                               group's largest round to nearest).  128 B per
+                               moment and row, as BF16.
                                The step count t saturates at 65535 (the
                                bias-correction factors are exactly 1 from step
-                               15936 on).  Not available with position noise, AIU
-                               or the active count.                               */
+                               15936 on).                                         */
 } gs_moment_prec;
 
 /* Regulariser form.  GS_REG_DAR is the paper's AdamW-GS (Eq. disentangled_adam);

@@ -219,13 +219,6 @@ float active_threshold()
     return c;
 }
 
-// The optional terms (noise, AIU, active count) run in the extended step,
-// which has no FP16-block variant.
-bool ext_unsupported(const gs_opt *o, const gs_step_params *p)
-{
-    return o->cfg.prec == GS_MOM_FP16_BLOCK && (p->noise || p->aiu || p->n_active);
-}
-
 void fill_args(const gs_opt *o, const gs_step_params *p, StepArgs *a)
 {
     memset(a, 0, sizeof(*a));
@@ -422,7 +415,6 @@ gs_status gs_step(gs_opt *o, const gs_attrs *attrs, const gs_grads *grads, const
     if (st != GS_OK) return st;
     const int64_t n = o->n_rows;
     if (!attrs || !grads || !params_ok(o, params)) return GS_ERR_INVALID_ARG;
-    if (ext_unsupported(o, params)) return GS_ERR_UNSUPPORTED;
     if (!attrs_ok(o, *attrs, n) || !attrs_ok(o, *grads, n) || !dev_ok(o, mask, mask ? (size_t)n : 0, 1))
         return GS_ERR_INVALID_ARG;
     StepArgs a;
@@ -440,7 +432,6 @@ gs_status gs_step_camera(gs_opt *o, const gs_attrs *attrs, const gs_grads *grads
     if (st != GS_OK) return st;
     const int64_t n = o->n_rows;
     if (!attrs || !grads || !camera_ok(cam) || !params_ok(o, params)) return GS_ERR_INVALID_ARG;
-    if (ext_unsupported(o, params)) return GS_ERR_UNSUPPORTED;
     if (!attrs_ok(o, *attrs, n) || !attrs_ok(o, *grads, n) || !dev_ok(o, mask_out, mask_out ? (size_t)n : 0, 1) ||
         !dev_ok(o, n_visible, n_visible ? 8 : 0, 8))
         return GS_ERR_INVALID_ARG;
@@ -461,7 +452,6 @@ gs_status gs_step_host(gs_opt *o, const gs_attrs *attrs, const gs_grads *gh, con
     if (st != GS_OK) return st;
     const int64_t n = o->n_rows;
     if (!attrs || !gh || !camera_ok(cam) || !params_ok(o, params) || !n_visible_host) return GS_ERR_INVALID_ARG;
-    if (ext_unsupported(o, params)) return GS_ERR_UNSUPPORTED;
     if (n && (!gh->xyz || !gh->scale || !gh->rot || !gh->opacity || !gh->sh)) return GS_ERR_INVALID_ARG;
     if (!attrs_ok(o, *attrs, n)) return GS_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -964,7 +954,6 @@ extern "C" gs_status gs_step_host_noalloc(gs_opt *o, const gs_attrs *attrs, cons
     const int64_t n = o->n_rows;
     if (n > (int64_t)kNaRows) return GS_ERR_INVALID_ARG;
     if (!attrs || !gh || !camera_ok(cam) || !params_ok(o, params) || !n_visible_host) return GS_ERR_INVALID_ARG;
-    if (ext_unsupported(o, params)) return GS_ERR_UNSUPPORTED;
     if (n && (!gh->xyz || !gh->scale || !gh->rot || !gh->opacity || !gh->sh)) return GS_ERR_INVALID_ARG;
     if (!attrs_ok(o, *attrs, n)) return GS_ERR_INVALID_ARG;
     float *base = noalloc_scratch(o->device);

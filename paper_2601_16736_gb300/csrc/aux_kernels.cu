@@ -233,7 +233,9 @@ __global__ void import_f16b_kernel(const StateView st, int32_t n, const float *_
         for (int q = 0; q < cnt; ++q) {
             int byte, group;
             f16b_slot(cols[q], byte, group);
-            *reinterpret_cast<uint16_t *>(row + byte) = (uint16_t)(e ? h_bits(x[q] * sc) : 0u);
+            uint32_t h = e ? h_bits(x[q] * sc) : 0u;
+            if (side && (h & 0x7fffu) == 0u && x[q] > 0.f) h = 1u;     // a positive v stays positive
+            *reinterpret_cast<uint16_t *>(row + byte) = (uint16_t)h;
         }
         row[kF16BExp + g] = (char)e;
     }

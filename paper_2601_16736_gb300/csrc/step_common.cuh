@@ -294,18 +294,27 @@ __device__ __forceinline__ uint32_t h2_rn(float x, float y)
     return *reinterpret_cast<const uint32_t *>(&h);
 }
 
-// Two values rounded stochastically: random bits (13 each) added below the
-// 10 mantissa bits FP16 keeps, then truncated by one conversion.  Exact
-// stochastic rounding for FP16 normals (values within 2^29 of the group's
-// largest); Inf and NaN pass unchanged.
+// Two second-moment values rounded stochastically: each is dithered by a
+// uniform offset of +-1/2 FP16 ulp (13 random bits, centred, added below the
+// 10 mantissa bits FP16 keeps), then both are rounded to nearest by one
+// conversion.  For FP16 normals (values within 2^29 of the group's largest)
+// that rounds up with probability equal to the discarded fraction; in FP16's
+// subnormal range the dither is below the quantum and values round to
+// nearest.  A positive value never becomes zero: v spans the square of m's
+// range, so a column with a gradient ~10^6 below its group's largest would
+// otherwise keep m != 0 beside v = 0, and a step that reuses the stored
+// moments (AIU) would divide by eps; it keeps the smallest subnormal
+// instead.  Zero, Inf and NaN pass unchanged.
 __device__ __forceinline__ uint32_t h2_sr(float x, float y, uint32_t rnd)
 {
     uint32_t ux = __float_as_uint(x), uy = __float_as_uint(y);
-    ux += (ux & 0x7f800000u) != 0x7f800000u ? (rnd & 0x1fffu) : 0u;
-    uy += (uy & 0x7f800000u) != 0x7f800000u ? ((rnd >> 16) & 0x1fffu) : 0u;
-    uint32_t d;
-    asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(__uint_as_float(uy)), "f"(__uint_as_float(ux)));
-    return d;
+    const uint32_t ex = ux & 0x7f800000u, ey = uy & 0x7f800000u;
+    ux += (ex != 0u && ex != 0x7f800000u) ? (rnd & 0x1fffu) - 0x1000u : 0u;
+    uy += (ey != 0u && ey != 0x7f800000u) ? ((rnd >> 16) & 0x1fffu) - 0x1000u : 0u;
+    uint32_t w = h2_rn(__uint_as_float(ux), __uint_as_float(uy));
+    if ((w & 0x7fffu) == 0u && x > 0.f) w |= 1u;
+    if ((w & 0x7fff0000u) == 0u && y > 0.f) w |= 1u << 16;
+    return w;
 }
 
 // n values -> (n + 1) / 2 packed words and the group exponent; m to nearest,

@@ -104,6 +104,117 @@ __device__ __forceinline__ void inv_sh_item(const StepArgs &a, const int32_t row
     }
 }
 
+// FP16-block rows: small item c = 12 (rotation) or 13 (xyz, scale, opacity
+// and t) of a listed row, with the optional terms as small_item_x.  Item 13
+// returns whether the row is active after the step.
+__device__ __forceinline__ bool small_item_x_f16b(const StepArgs &a, const int32_t row, const int c, const bool vis,
+                                                  const uint8_t fl, const float2 f, const float3 nz)
+{
+    using S = State<GS_MOM_FP16_BLOCK>;
+    const bool aiu = !vis && (fl & kFAiu);
+    char *mr = S::row(a.m, row), *vr = S::row(a.v, row);
+    const size_t r = (size_t)row;
+    if (c == 12) {
+        const uint2 um = *reinterpret_cast<const uint2 *>(mr + kF16BRot), uv = *reinterpret_cast<const uint2 *>(vr + kF16BRot);
+        const uint32_t wm[2] = {um.x, um.y}, wv[2] = {uv.x, uv.y};
+        float m[4], v[4];
+        decode_w<4>(wm, dec_scale((uint8_t)mr[kF16BExp + 6]), m);
+        decode_w<4>(wv, dec_scale((uint8_t)vr[kF16BExp + 6]), v);
+        if (vis || aiu) {
+            float *pt = a.a_rot + r * 4;
+            float4 th = ld4(pt);
+            const float l = a.lr[2];
+            if (vis) {
+                const float4 g = ldg4_stream(a.g_rot + r * 4);
+                th.x = step_element(th.x, g.x, m[0], v[0], f.x, f.y, a, l, false, 0.f, 0.f, 0.f);
+                th.y = step_element(th.y, g.y, m[1], v[1], f.x, f.y, a, l, false, 0.f, 0.f, 0.f);
+                th.z = step_element(th.z, g.z, m[2], v[2], f.x, f.y, a, l, false, 0.f, 0.f, 0.f);
+                th.w = step_element(th.w, g.w, m[3], v[3], f.x, f.y, a, l, false, 0.f, 0.f, 0.f);
+            } else {
+                const float la = l * a.aiu_scale;
+                th.x = aiu_element(th.x, m[0], v[0], f, a.eps, la);
+                th.y = aiu_element(th.y, m[1], v[1], f, a.eps, la);
+                th.z = aiu_element(th.z, m[2], v[2], f, a.eps, la);
+                th.w = aiu_element(th.w, m[3], v[3], f, a.eps, la);
+            }
+            st4(pt, th);
+        }
+        if (vis || (fl & kFRsr)) {             // an AIU step keeps the moments
+            if (fl & kFRsr) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    m[q] *= a.alpha1;
+                    v[q] *= a.alpha2;
+                }
+            }
+            uint32_t hm[2], hv[2];
+            const uint32_t em = encode_rn_w<4>(m, hm), ev = encode_sr_w<4>(v, hv, a, row, 6);
+            __stcs(reinterpret_cast<uint2 *>(mr + kF16BRot), make_uint2(hm[0], hm[1]));
+            __stcs(reinterpret_cast<uint2 *>(vr + kF16BRot), make_uint2(hv[0], hv[1]));
+            mr[kF16BExp + 6] = (char)em;
+            vr[kF16BExp + 6] = (char)ev;
+        }
+        return false;
+    }
+    const uint4 um = *reinterpret_cast<const uint4 *>(mr + kF16BXso), uv = *reinterpret_cast<const uint4 *>(vr + kF16BXso);
+    const uint32_t wm[4] = {um.x, um.y, um.z, um.w & 0xffffu}, wv[4] = {uv.x, uv.y, uv.z, uv.w};
+    float m[7], v[7];
+    decode_w<7>(wm, dec_scale((uint8_t)mr[kF16BExp + 7]), m);
+    decode_w<7>(wv, dec_scale((uint8_t)vr[kF16BExp + 7]), v);
+    uint32_t t = um.w >> 16;
+    float *px = a.a_xyz + r * 3, *ps = a.a_scale + r * 3, *po = a.a_op + r;
+    float x0 = px[0], x1 = px[1], x2 = px[2], s0 = ps[0], s1 = ps[1], s2 = ps[2], op = *po;
+    if (vis) {
+        const float *gx = a.g_xyz + r * 3, *gs = a.g_scale + r * 3;
+        const float g0 = __ldcs(gx), g1 = __ldcs(gx + 1), g2 = __ldcs(gx + 2);
+        const float gs0 = __ldcs(gs), gs1 = __ldcs(gs + 1), gs2 = __ldcs(gs + 2), go = __ldcs(a.g_op + r);
+        const bool ds = a.dar_s != 0, dop = a.dar_o != 0;
+        // regulariser derivatives at the old values (App. Eqs. scale, opacity)
+        const float r0s = ds ? expf(s0) : 0.f, r1s = ds ? expf(s1) : 0.f, r2s = ds ? expf(s2) : 0.f;
+        const float rop = dop ? dsigmoid(op) : 0.f;
+        x0 = step_element(x0, g0, m[0], v[0], f.x, f.y, a, a.lr[0], false, 0.f, 0.f, 0.f);
+        x1 = step_element(x1, g1, m[1], v[1], f.x, f.y, a, a.lr[0], false, 0.f, 0.f, 0.f);
+        x2 = step_element(x2, g2, m[2], v[2], f.x, f.y, a, a.lr[0], false, 0.f, 0.f, 0.f);
+        s0 = step_element(s0, gs0, m[3], v[3], f.x, f.y, a, a.lr[1], ds, r0s, a.lam_s, a.clip_s);
+        s1 = step_element(s1, gs1, m[4], v[4], f.x, f.y, a, a.lr[1], ds, r1s, a.lam_s, a.clip_s);
+        s2 = step_element(s2, gs2, m[5], v[5], f.x, f.y, a, a.lr[1], ds, r2s, a.lam_s, a.clip_s);
+        op = step_element(op, go, m[6], v[6], f.x, f.y, a, a.lr[3], dop, rop, a.lam_o, a.clip_o);
+        t = min(t + 1u, 65535u);                // the row's own step count (Sec. 3.2)
+    } else if (aiu) {
+        const float lx = a.lr[0] * a.aiu_scale, ls = a.lr[1] * a.aiu_scale;
+        x0 = aiu_element(x0, m[0], v[0], f, a.eps, lx);
+        x1 = aiu_element(x1, m[1], v[1], f, a.eps, lx);
+        x2 = aiu_element(x2, m[2], v[2], f, a.eps, lx);
+        s0 = aiu_element(s0, m[3], v[3], f, a.eps, ls);
+        s1 = aiu_element(s1, m[4], v[4], f, a.eps, ls);
+        s2 = aiu_element(s2, m[5], v[5], f, a.eps, ls);
+        op = aiu_element(op, m[6], v[6], f, a.eps, a.lr[3] * a.aiu_scale);
+    }
+    if (vis || (fl & kFRsr)) {
+        if (fl & kFRsr) {
+#pragma unroll
+            for (int q = 0; q < 7; ++q) {
+                m[q] *= a.alpha1;
+                v[q] *= a.alpha2;
+            }
+        }
+        uint32_t hm[4], hv[4];
+        const uint32_t em = encode_rn_w<7>(m, hm), ev = encode_sr_w<7>(v, hv, a, row, 0);
+        __stcs(reinterpret_cast<uint4 *>(mr + kF16BXso), make_uint4(hm[0], hm[1], hm[2], hm[3] | t << 16));
+        __stcs(reinterpret_cast<uint4 *>(vr + kF16BXso), make_uint4(hv[0], hv[1], hv[2], hv[3]));
+        mr[kF16BExp + 7] = (char)em;
+        vr[kF16BExp + 7] = (char)ev;
+    }
+    if (vis || aiu) {
+        __stcs(ps, s0); __stcs(ps + 1, s1); __stcs(ps + 2, s2);
+        __stcs(po, op);
+    }
+    if (vis || aiu || (fl & kFNoise)) {
+        __stcs(px, x0 - nz.x); __stcs(px + 1, x1 - nz.y); __stcs(px + 2, x2 - nz.z);
+    }
+    return op > a.tau_act;
+}
+
 // Small item c of a listed row, as small_item of the plain step, with the
 // optional terms.  vis: Sparse Adam + DAR, t += 1 (where chunk 14 keeps t);
 // otherwise kFAiu: the AIU step from the current moments.  kFRsr scales the
@@ -113,6 +224,9 @@ template <int kPrec>
 __device__ __forceinline__ bool small_item_x(const StepArgs &a, const int32_t row, const int c, const bool vis,
                                              const uint8_t fl, const float2 f, const float3 nz)
 {
+    if constexpr (kPrec == GS_MOM_FP16_BLOCK) {
+        return small_item_x_f16b(a, row, c, vis, fl, f, nz);
+    } else {
     using S = State<kPrec>;
     const bool aiu = !vis && (fl & kFAiu);
     Chunk k = S::load_small(a, row, c);
@@ -196,6 +310,7 @@ __device__ __forceinline__ bool small_item_x(const StepArgs &a, const int32_t ro
     }
     if (vis || (fl & kFRsr)) S::store_small(a, row, c, k);    // an AIU step keeps the moments
     return active;
+    }
 }
 
 // Shared-memory lists of one tile of the extended step.
@@ -250,9 +365,11 @@ __device__ __forceinline__ void tile_decide_x(const StepArgs &a, const int vis_s
             if (a.restate && stss_sampled(a, (int32_t)row)) fl |= kFRsr;
             if (a.noise == GS_NOISE_ALL || (a.noise == GS_NOISE_VISIBLE && vis)) fl |= kFNoise;
             const bool aiu_draw = a.aiu && !vis && aiu_sampled(a, (int32_t)row);
-            if ((vis || aiu_draw) && !a.bias_mode)
-                t_old[j] = *reinterpret_cast<const uint32_t *>(static_cast<const char *>(a.m) +
-                                                               (size_t)row * kRowBytes + kTByte);
+            if ((vis || aiu_draw) && !a.bias_mode) {
+                const char *tp = static_cast<const char *>(a.m) + (size_t)row * kRowBytes + kTByte;
+                if constexpr (kTByte % 4 == 0) t_old[j] = *reinterpret_cast<const uint32_t *>(tp);
+                else t_old[j] = *reinterpret_cast<const uint16_t *>(tp);      // FP16-block rows: uint16 t
+            }
             // a primitive never seen has no moments: its AIU step is zero
             if (aiu_draw && (a.bias_mode || t_old[j] > 0u)) fl |= kFAiu;
             in_i = !vis && (fl & (kFRsr | kFAiu));
@@ -333,7 +450,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) step_tile_x(const StepAr
     tile_decide_x<kTile, S::kRowBytes, S::kTByte>(a, vis_src, r0, L, nv, ni);
 
     unsigned my_active = 0;
-    const int e_sh = kNsh * nv, e_vis = e_sh + 3 * nv, e_ish = e_vis + kNsh * ni, e_all = e_ish + 3 * ni;
+    constexpr int kSmall = kSmallItems<kPrec>, kOpItem = 11 + kSmall;     // the item holding the opacity
+    const int e_sh = kNsh * nv, e_vis = e_sh + kSmall * nv, e_ish = e_vis + kNsh * ni, e_all = e_ish + kSmall * ni;
     for (int w = threadIdx.x; w < e_all; w += kThreads) {
         if (w < e_sh) {
             const int j = w / kNsh, i = w - j * kNsh;
@@ -342,7 +460,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) step_tile_x(const StepAr
             const int q = w - e_sh;
             const int j = q % nv, c = 12 + q / nv;
             const bool act = small_item_x<kPrec>(a, L.list[j], c, true, L.vflag[j], L.fac[j], L.nz[j]);
-            my_active += (c == 14 && act) ? 1u : 0u;
+            my_active += (c == kOpItem && act) ? 1u : 0u;
         } else if (w < e_ish) {
             const int q = w - e_vis;
             const int j = q / kNsh, i = q - j * kNsh;
@@ -351,7 +469,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) step_tile_x(const StepAr
             const int q = w - e_ish;
             const int j = q % ni, c = 12 + q / ni;
             const bool act = small_item_x<kPrec>(a, L.ilist[j], c, false, L.iflag[j], L.ifac[j], L.inz[j]);
-            my_active += (c == 14 && act) ? 1u : 0u;
+            my_active += (c == kOpItem && act) ? 1u : 0u;
         }
     }
     if (a.n_active) {
@@ -380,6 +498,9 @@ cudaError_t launch_step_ext(const StepArgs &a, int prec, int vis_src, cudaStream
         break;
     case GS_MOM_BF16_HYBRID:
         step_tile_x<kExtTile, kExtMinBlocks, GS_MOM_BF16_HYBRID, 8><<<grid, kThreads, 0, s>>>(a, vis_src);
+        break;
+    case GS_MOM_FP16_BLOCK:
+        step_tile_x<kExtTile, kExtMinBlocks, GS_MOM_FP16_BLOCK, 8><<<grid, kThreads, 0, s>>>(a, vis_src);
         break;
     default:
         return cudaErrorNotSupported;

@@ -54,9 +54,10 @@ def _group_exponent(blk):
     return np.where(e < 15, 0, e)
 
 
-def _f16b(x):
+def _f16b(x, second_moment=False):
     """The FP16-block encoding restated: per row and group, the largest biased
-    FP32 exponent e; values stored as FP16 (nearest) of x * 2^(141 - e)."""
+    FP32 exponent e; values stored as FP16 (nearest) of x * 2^(141 - e); a
+    positive second moment keeps at least the smallest FP16 subnormal."""
     x = np.ascontiguousarray(x, np.float32)
     out = np.zeros_like(x)
     for cols in F16B_GROUPS:
@@ -64,6 +65,8 @@ def _f16b(x):
         e = _group_exponent(x[:, cols])
         sc = np.where(e > 0, np.ldexp(1.0, 141 - e), 0.0)
         h = (blk * sc[:, None]).astype(np.float32).astype(np.float16)
+        if second_moment:
+            h = np.where((h == 0) & (blk > 0) & (e[:, None] > 0), np.float16(2.0 ** -24), h)
         dec = np.where(e > 0, np.ldexp(1.0, e - 141), 0.0)
         out[:, cols] = (h.astype(np.float64) * dec[:, None]).astype(np.float32)
     return out
@@ -149,7 +152,7 @@ def test_export_import_and_reindex(G, orc, prec):
                           torch.from_numpy(t.view(np.int32)).cuda())
     m2, v2, t2 = run.state()
     if prec == "FP16_BLOCK":
-        em, ev = _f16b(m), _f16b(v)
+        em, ev = _f16b(m), _f16b(v, second_moment=True)
     else:
         em, ev = _bf16(m), _bf16(v)
     if prec == "BF16_HYBRID":
@@ -207,18 +210,33 @@ def test_3m_1000_steps_sampled(G, orc, prec, gate):
         assert e <= gate, f"{prec} group {g}: {e:.2e} > {gate:.0e}"
 
 
-def test_fp16_block_rejects_optional_terms(G):
-    """FP16-block moments have no extended-step variant: those requests are
-    refused before anything is launched, and the context stays usable."""
-    n = 1000
-    run = GpuRun(synth.scene_uniform(n, 930), prec=G.GS_MOM_FP16_BLOCK)
-    mask = torch.ones(n, dtype=torch.uint8, device="cuda")
+def test_fp16_block_with_optional_terms(G, orc):
+    """Noise on every row, AIU, RSR and the active count with FP16-block
+    moments: attributes follow the oracle to the mixed-precision bound, and
+    the count equals the classification of the GPU's own logits."""
+    n = 20_011
+    groups = synth.scene_uniform(n, 930)
+    run = GpuRun(groups, prec=G.GS_MOM_FP16_BLOCK)
+    st = orc.State(synth.to_rows(groups))
+    cfg = orc.Config(n_i=orc.dar_normaliser(800 * 800))
+    rng = np.random.default_rng(931)
     na = torch.zeros(1, dtype=torch.int64, device="cuda")
-    for kw in (dict(noise=1), dict(aiu=True, aiu_prob=0.1), dict(n_active=na)):
-        with pytest.raises(G.GsError) as e:
-            run.step_mask(mask, G.make_params(LR, 1, **kw))
-        assert e.value.status == G.GS_ERR_UNSUPPORTED
-    run.step_mask(mask, G.make_params(LR, 1))         # the plain step still runs
-    torch.cuda.synchronize()
-    assert G.gs_opt_sync_errors(run.h) == G.GS_OK
+    for k in range(1, 7):
+        g = synth.grads_rows(n, 932, k)
+        mask = (rng.random(n) < 0.4).astype(np.uint8)
+        kw = dict(noise=2, noise_lr=50.0, noise_k=3.0, noise_t=0.5, aiu=k > 2, aiu_prob=0.3, aiu_scale=0.5)
+        ext = orc.Ext(noise_mode=2, aiu=k > 2, noise_lr=50.0, noise_k=3.0, noise_t=0.5, aiu_prob=0.3,
+                      aiu_scale=0.5, seed=13)
+        rs = k == 4
+        run.set_grads(g)
+        na.zero_()
+        run.step_mask(torch.from_numpy(mask).cuda(),
+                      G.make_params(LR, k, restate=rs, restate_ratio=0.4, seed=13, n_active=na, **kw))
+        orc.step_ext(cfg, st, g, mask, LR, True, True, k, ext)
+        if rs:
+            orc.restate(cfg, st, 13, k, 0.4)
+        assert int(na.item()) == orc.active_rows(run.attrs["opacity"].cpu().numpy().ravel()).size
+    assert_close(run.rows(), st.theta, 2e-3, what="FP16 block with noise, AIU, RSR")
+    _, _, t = run.state()
+    assert np.array_equal(t, st.t)
     run.close()

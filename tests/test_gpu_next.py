@@ -73,7 +73,7 @@ def test_extended_kernel_without_terms_is_the_plain_step(G):
     b.close()
 
 
-@pytest.mark.parametrize("prec", ["FP32", "BF16_HYBRID"])
+@pytest.mark.parametrize("prec", ["FP32", "BF16_HYBRID", "FP16_BLOCK"])
 @pytest.mark.parametrize("mode", [1, 2])
 def test_noise_matches_oracle(G, orc, prec, mode):
     n = 30_007
@@ -125,7 +125,7 @@ def test_noise_only_rows_move_by_the_noise_term(G, orc):
     run.close()
 
 
-@pytest.mark.parametrize("prec", ["FP32", "BF16_HYBRID"])
+@pytest.mark.parametrize("prec", ["FP32", "BF16_HYBRID", "FP16_BLOCK"])
 @pytest.mark.parametrize("bias_mode", [0, 1])
 def test_aiu_matches_oracle(G, orc, prec, bias_mode):
     n = 25_013
