@@ -57,7 +57,7 @@ typedef enum gs_status {
     GS_ERR_INVALID_ARG = 1, /* bad pointer, size, alignment or value; nothing launched */
     GS_ERR_CUDA = 2,        /* a CUDA runtime/driver call failed; context latched   */
     GS_ERR_OOM = 3,         /* device allocation failed                               */
-    GS_ERR_UNSUPPORTED = 4, /* valid request this build does not implement            */
+    GS_ERR_UNSUPPORTED = 4, /* valid request the library does not implement          */
     GS_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up                     */
     GS_ERR_STATE = 6        /* context latched by an earlier error                    */
 } gs_status;

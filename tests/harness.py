@@ -37,7 +37,7 @@ def assert_close(got_rows, ref_rows, rel: float, elem: float | None = None, rows
     return errs
 
 
-class GpuRun:
+class GpuScene:
     """Attributes, gradients and an optimizer context on cuda:0."""
 
     def __init__(self, groups: dict, cfg=None, **cfg_kw):

@@ -6,7 +6,7 @@ turn) and through the captured graph — and match the FP64 oracle."""
 import numpy as np
 import pytest
 
-from harness import GpuRun, OracleRun, assert_close
+from harness import GpuScene, OracleRun, assert_close
 from paper_2601_16736_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -30,8 +30,8 @@ def _scenes(prec_name, G):
     runs_b, runs_s, cams = [], [], []
     for i, n in enumerate(SIZES):
         groups = synth.scene_blobs(n, 1200 + i, [6.0, 12.5, 22.0, 40.0, 75.0][i])
-        rb = GpuRun(groups, prec=getattr(G, "GS_MOM_" + prec_name))
-        rs = GpuRun(groups, prec=getattr(G, "GS_MOM_" + prec_name))
+        rb = GpuScene(groups, prec=getattr(G, "GS_MOM_" + prec_name))
+        rs = GpuScene(groups, prec=getattr(G, "GS_MOM_" + prec_name))
         g = synth.grads_rows(n, 1300 + i)
         rb.set_grads(g)
         rs.set_grads(g)
@@ -75,7 +75,7 @@ def test_batch_matches_oracle(G, orc):
     runs, refs, cams = [], [], []
     for i, n in enumerate(sizes):
         groups = synth.scene_blobs(n, 1400 + i, 12.5)
-        runs.append(GpuRun(groups))
+        runs.append(GpuScene(groups))
         refs.append(OracleRun(orc, synth.to_rows(groups)))
         cams.append(synth.ring_cameras(6, (0.0, 30.0)))
     b = G.gs_batch_create([r.h for r in runs])
@@ -98,8 +98,8 @@ def test_batch_matches_oracle(G, orc):
 
 
 def test_batch_rejects_bad_sets(G):
-    a = GpuRun(synth.scene_uniform(100, 1600))
-    c = GpuRun(synth.scene_uniform(100, 1601), prec=G.GS_MOM_BF16)
+    a = GpuScene(synth.scene_uniform(100, 1600))
+    c = GpuScene(synth.scene_uniform(100, 1601), prec=G.GS_MOM_BF16)
     with pytest.raises(G.GsError):                 # mixed moment precisions
         G.gs_batch_create([a.h, c.h])
     with pytest.raises(G.GsError):                 # more than GS_MAX_BATCH scenes

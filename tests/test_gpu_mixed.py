@@ -18,7 +18,7 @@ bound 3e-2 only guards against regressions.
 import numpy as np
 import pytest
 
-from harness import GpuRun, OracleRun, assert_close, group_errors
+from harness import GpuScene, OracleRun, assert_close, group_errors
 from paper_2601_16736_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -97,7 +97,7 @@ def test_one_step(G, orc, prec):
     groups = synth.scene_blobs(n, 901, 12.5)
     grads = synth.grads_rows(n, 902)
     cam = synth.ring_cameras(8)[2]
-    run = GpuRun(groups, prec=getattr(G, "GS_MOM_" + prec))
+    run = GpuScene(groups, prec=getattr(G, "GS_MOM_" + prec))
     run.set_grads(grads)
     run.step_camera(cam, G.make_params(LR, 100, restate=True, restate_ratio=0.3, seed=9))
     got = run.rows()
@@ -124,7 +124,7 @@ def test_one_step(G, orc, prec):
 def test_edge_sizes(G, orc, prec, n):
     groups = synth.scene_uniform(n, 910 + n)
     rng = np.random.default_rng(n)
-    run = GpuRun(groups, prec=getattr(G, "GS_MOM_" + prec))
+    run = GpuScene(groups, prec=getattr(G, "GS_MOM_" + prec))
     ref = OracleRun(orc, synth.to_rows(groups))
     for k in (1, 2, 3, 100):
         grads = synth.grads_rows(n, 911, k)
@@ -143,7 +143,7 @@ def test_edge_sizes(G, orc, prec, n):
 @pytest.mark.parametrize("prec", LOWP)
 def test_export_import_and_reindex(G, orc, prec):
     n = 20_001
-    run = GpuRun(synth.scene_uniform(n, 920), prec=getattr(G, "GS_MOM_" + prec))
+    run = GpuScene(synth.scene_uniform(n, 920), prec=getattr(G, "GS_MOM_" + prec))
     rng = np.random.default_rng(921)
     m = rng.normal(size=(n, 59)).astype(np.float32)
     v = rng.random((n, 59)).astype(np.float32)
@@ -173,7 +173,7 @@ def _run_sampled(G, orc, wl, prec, sample):
     cams = wl.cameras()
     order = synth.view_order(len(cams), wl.steps, wl.seed)
     grads_host = [synth.grads_rows(wl.n, wl.seed, b) for b in range(wl.grad_buffers)]
-    run = GpuRun(groups, prec=getattr(G, "GS_MOM_" + prec))
+    run = GpuScene(groups, prec=getattr(G, "GS_MOM_" + prec))
     gdev = [{k: torch.from_numpy(v).cuda() for k, v in synth.from_rows(gh).items()} for gh in grads_host]
     ids_t = torch.from_numpy(sample).cuda()
     ref = OracleRun(orc, synth.to_rows(groups)[sample], row_ids=sample)
@@ -216,7 +216,7 @@ def test_fp16_block_with_optional_terms(G, orc):
     the count equals the classification of the GPU's own logits."""
     n = 20_011
     groups = synth.scene_uniform(n, 930)
-    run = GpuRun(groups, prec=G.GS_MOM_FP16_BLOCK)
+    run = GpuScene(groups, prec=G.GS_MOM_FP16_BLOCK)
     st = orc.State(synth.to_rows(groups))
     cfg = orc.Config(n_i=orc.dar_normaliser(800 * 800))
     rng = np.random.default_rng(931)

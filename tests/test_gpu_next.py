@@ -11,7 +11,7 @@ must equal the oracle's classification of the GPU's own FP32 logits."""
 import numpy as np
 import pytest
 
-from harness import GpuRun, assert_close
+from harness import GpuScene, assert_close
 from paper_2601_16736_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -55,8 +55,8 @@ def test_extended_kernel_without_terms_is_the_plain_step(G):
     plain kernel's results bit for bit (same per-element arithmetic)."""
     n = 20_011
     groups = synth.scene_uniform(n, 1900)
-    a = GpuRun(groups)
-    b = GpuRun(groups)
+    a = GpuScene(groups)
+    b = GpuScene(groups)
     na = torch.zeros(1, dtype=torch.int64, device="cuda")
     rng = np.random.default_rng(1901)
     for k in range(1, 6):
@@ -78,7 +78,7 @@ def test_extended_kernel_without_terms_is_the_plain_step(G):
 def test_noise_matches_oracle(G, orc, prec, mode):
     n = 30_007
     groups = _noisy_scene(n, 1910)
-    run = GpuRun(groups, prec=getattr(G, "GS_MOM_" + prec))
+    run = GpuScene(groups, prec=getattr(G, "GS_MOM_" + prec))
     st = orc.State(synth.to_rows(groups))
     cfg = orc.Config(n_i=orc.dar_normaliser(800 * 800))
     rng = np.random.default_rng(1911)
@@ -112,7 +112,7 @@ def test_noise_only_rows_move_by_the_noise_term(G, orc):
     change is exactly the noise term (visible and, in mode 2, invisible)."""
     n = 5_003
     groups = _noisy_scene(n, 1920)
-    run = GpuRun(groups)
+    run = GpuScene(groups)
     mask = (np.arange(n) % 2).astype(np.uint8)
     o, ext = _ext(G, orc, noise=2, noise_lr=100.0, noise_k=3.0, noise_t=0.5)
     run.step_mask(torch.from_numpy(mask).cuda(), G.make_params(LR, 1, dar_opacity=False, dar_scale=False, seed=3,
@@ -130,7 +130,7 @@ def test_noise_only_rows_move_by_the_noise_term(G, orc):
 def test_aiu_matches_oracle(G, orc, prec, bias_mode):
     n = 25_013
     groups = synth.scene_uniform(n, 1930)
-    run = GpuRun(groups, prec=getattr(G, "GS_MOM_" + prec), bias_mode=bias_mode)
+    run = GpuScene(groups, prec=getattr(G, "GS_MOM_" + prec), bias_mode=bias_mode)
     st = orc.State(synth.to_rows(groups))
     cfg = orc.Config(n_i=orc.dar_normaliser(800 * 800), bias_mode=bias_mode)
     rng = np.random.default_rng(1931)
@@ -166,7 +166,7 @@ def test_active_count_all_paths(G, orc):
     rows); it must equal the classification of the GPU's own logits."""
     n = 40_009
     groups = _noisy_scene(n, 1940)
-    run = GpuRun(groups)
+    run = GpuScene(groups)
     na = torch.zeros(1, dtype=torch.int64, device="cuda")
     rng = np.random.default_rng(1941)
     for k in range(1, 7):
@@ -216,7 +216,7 @@ def test_prune_dead_rows_through_reindex(G, orc):
     gather the attributes with it, then compare with the oracle."""
     n = 50_021
     groups = _noisy_scene(n, 1960)
-    run = GpuRun(groups)
+    run = GpuScene(groups)
     run.set_grads(synth.grads_rows(n, 1961))
     run.step_mask(torch.ones(n, dtype=torch.uint8, device="cuda"), G.make_params(LR, 1))
     m0, v0, t0 = run.state()
@@ -245,7 +245,7 @@ def test_prune_dead_rows_through_reindex(G, orc):
 
 
 def test_batch_rejects_extended_terms(G):
-    a = GpuRun(synth.scene_uniform(100, 1970))
+    a = GpuScene(synth.scene_uniform(100, 1970))
     b = G.gs_batch_create([a.h])
     for kw in (dict(noise=1), dict(aiu=True, aiu_prob=0.1),
                dict(n_active=torch.zeros(1, dtype=torch.int64, device="cuda"))):
@@ -259,7 +259,7 @@ def test_batch_rejects_extended_terms(G):
 
 
 def test_extended_params_validated(G):
-    a = GpuRun(synth.scene_uniform(10, 1980))
+    a = GpuScene(synth.scene_uniform(10, 1980))
     bad = [dict(noise=3), dict(noise=1, noise_lr=float("nan")), dict(aiu=True, aiu_prob=1.5),
            dict(aiu=True, aiu_prob=0.5, aiu_scale=float("inf"))]
     for kw in bad:

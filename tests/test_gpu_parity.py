@@ -9,7 +9,7 @@ compared bit-exactly.
 import numpy as np
 import pytest
 
-from harness import GpuRun, OracleRun, assert_close, group_errors
+from harness import GpuScene, OracleRun, assert_close, group_errors
 from paper_2601_16736_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -36,7 +36,7 @@ def test_visibility_bit_exact(G, orc, scene):
     n = 250_001
     groups = synth.scene_uniform(n, 91) if scene == "uniform" else synth.scene_blobs(n, 92, 12.5)
     xyz = torch.from_numpy(groups["xyz"]).cuda()
-    run = GpuRun(groups)
+    run = GpuScene(groups)
     mask = torch.zeros(n, dtype=torch.uint8, device="cuda")
     rows = torch.full((n,), -1, dtype=torch.int32, device="cuda")
     cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
@@ -67,7 +67,7 @@ def test_one_step_parity(G, orc, scene, restate):
     groups = synth.scene_uniform(n, 101) if scene == "uniform" else synth.scene_blobs(n, 102, 12.5)
     grads = synth.grads_rows(n, 103)
     cam = synth.ring_cameras(8)[3]
-    run = GpuRun(groups)
+    run = GpuScene(groups)
     run.set_grads(grads)
     p = G.make_params(LR, 100, restate=restate, restate_ratio=0.3, seed=7)
     run.step_camera(cam, p)
@@ -105,7 +105,7 @@ def test_edge_sizes_and_masks(G, orc, n, pattern):
         mask_np[n - 1] = 1
     else:
         mask_np = (rng.random(n) < 0.5).astype(np.uint8)
-    run = GpuRun(groups)
+    run = GpuScene(groups)
     run.set_grads(grads)
     ref = OracleRun(orc, synth.to_rows(groups))
     mask_t = None if mask_np is None else torch.from_numpy(mask_np).cuda()
@@ -127,7 +127,7 @@ def test_edge_sizes_and_masks(G, orc, n, pattern):
 def test_global_bias_mode(G, orc):
     n = 5000
     groups = synth.scene_blobs(n, 401, 12.5)
-    run = GpuRun(groups, bias_mode=1)
+    run = GpuScene(groups, bias_mode=1)
     ref = OracleRun(orc, synth.to_rows(groups), bias_mode=1)
     rng = np.random.default_rng(402)
     for k in range(1, 31):
@@ -146,7 +146,7 @@ def test_regulariser_variants(G, orc, reg_mode):
     kw = dict(reg_mode=reg_mode)
     if reg_mode == 3:
         kw["lambda_o"] = 50.0                    # so the clip is active
-    run = GpuRun(groups, **kw)
+    run = GpuScene(groups, **kw)
     ref = OracleRun(orc, synth.to_rows(groups), **kw)
     rng = np.random.default_rng(600)
     for k in range(1, 11):
@@ -170,7 +170,7 @@ def _run_sequence(G, orc, wl, n_steps, sample=None):
     n = wl.n
     nbuf = wl.grad_buffers
     grads_host = [synth.grads_rows(n, wl.seed, b) for b in range(nbuf)]
-    run = GpuRun(groups)
+    run = GpuScene(groups)
     gdev = []
     for gh in grads_host:
         gdev.append({k: torch.from_numpy(v).cuda() for k, v in synth.from_rows(gh).items()})
@@ -236,7 +236,7 @@ def _random_state(n, seed):
 
 def test_export_import_roundtrip(G):
     n = 3001
-    run = GpuRun(synth.scene_uniform(n, 700))
+    run = GpuScene(synth.scene_uniform(n, 700))
     m, v, t = _random_state(n, 701)
     G.gs_opt_import_state(run.h, torch.from_numpy(m).cuda(), torch.from_numpy(v).cuda(),
                           torch.from_numpy(t.view(np.int32)).cuda())
@@ -248,7 +248,7 @@ def test_export_import_roundtrip(G):
 @pytest.mark.parametrize("n_new_kind", ["same", "grow", "shrink"])
 def test_reindex_matches_oracle(G, orc, n_new_kind):
     n = 50_000
-    run = GpuRun(synth.scene_uniform(n, 710))
+    run = GpuScene(synth.scene_uniform(n, 710))
     m, v, t = _random_state(n, 711)
     G.gs_opt_import_state(run.h, torch.from_numpy(m).cuda(), torch.from_numpy(v).cuda(),
                           torch.from_numpy(t.view(np.int32)).cuda())
@@ -273,7 +273,7 @@ def test_reindex_matches_oracle(G, orc, n_new_kind):
 
 def test_reindex_out_of_range_is_reported_not_read(G):
     n = 1000
-    run = GpuRun(synth.scene_uniform(n, 720))
+    run = GpuScene(synth.scene_uniform(n, 720))
     src = np.arange(n, dtype=np.int32)
     src[17] = n + 5
     G.gs_reindex_state(run.h, torch.from_numpy(src).cuda(), None, n)
@@ -287,7 +287,7 @@ def test_reindex_out_of_range_is_reported_not_read(G):
 @pytest.mark.parametrize("n", [1, 17, 7001])
 def test_gather_attrs(G, n):
     groups = synth.scene_uniform(n, 730 + n)
-    run = GpuRun(groups)
+    run = GpuScene(groups)
     src, reset, attr_src = synth.reindex_event(n, 731, 0)
     attr_src = attr_src.copy()
     if attr_src.size > 2:
@@ -319,7 +319,7 @@ def test_gather_attrs(G, n):
 
 
 def test_bias_table_matches_oracle(G, orc):
-    run = GpuRun(synth.scene_uniform(10, 740))
+    run = GpuScene(synth.scene_uniform(10, 740))
     L = G.gs_bias_table_len(run.h)
     # first k at which both FP32 factors are exactly 1: 1/sqrt(1 - 0.999^k)
     # rounds to 1.0f once 0.999^k <= 2^-23, i.e. from k ~ 15936 on
@@ -345,7 +345,7 @@ def test_step_host_equals_device_path(G, pinned):
     groups = synth.scene_blobs(n, 750, 12.5)
     grads = synth.grads_rows(n, 751)
     cam = synth.ring_cameras(5)[2]
-    a, b = GpuRun(groups), GpuRun(groups)
+    a, b = GpuScene(groups), GpuScene(groups)
     a.set_grads(grads)
     p = G.make_params(LR, 1)
     a.step_camera(cam, p)
@@ -364,7 +364,7 @@ def test_step_host_equals_device_path(G, pinned):
 def test_invalid_arguments_are_rejected(G):
     n = 1000
     groups = synth.scene_uniform(n, 760)
-    run = GpuRun(groups)
+    run = GpuScene(groups)
     A, Gr = G.make_attrs(run.attrs), G.make_attrs(run.grads)
     cam = G.make_camera(synth.ring_cameras(4)[0])
     ok = G.make_params(LR, 1)

@@ -13,7 +13,7 @@ trajectories stay comparable on every row."""
 import numpy as np
 import pytest
 
-from harness import GpuRun, OracleRun, assert_close, group_errors
+from harness import GpuScene, OracleRun, assert_close, group_errors
 from paper_2601_16736_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -45,7 +45,7 @@ def test_steps_with_reindex_events(G, orc, prec):
     groups = synth.scene_blobs(n, seed, 12.5)
     cams = synth.ring_cameras(20, (-15.0, 0.0, 15.0))
     order = synth.view_order(len(cams), steps, seed)
-    run = GpuRun(groups, prec=getattr(G, "GS_MOM_" + prec))
+    run = GpuScene(groups, prec=getattr(G, "GS_MOM_" + prec))
     ref = OracleRun(orc, synth.to_rows(groups))
     adopted = 0
     for k in range(1, steps + 1):

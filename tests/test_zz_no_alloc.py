@@ -11,7 +11,7 @@ process.
 import numpy as np
 import pytest
 
-from harness import GpuRun, assert_close
+from harness import GpuScene, assert_close
 from paper_2601_16736_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -33,7 +33,7 @@ def test_noalloc_step_matches_allocating_step(G):
     n = 50_001                       # ~98 tiles of 512 rows and a ragged tail
     groups = synth.scene_blobs(n, 880, 12.5)
     cams = synth.ring_cameras(8, (0.0, 30.0))
-    ref, new = GpuRun(groups), GpuRun(groups)
+    ref, new = GpuScene(groups), GpuScene(groups)
     for call in range(2):            # two calls in a row: the array keeps the first call's contents
         k = call + 1
         grads = synth.grads_rows(n, 881, call)
@@ -55,7 +55,7 @@ def test_noalloc_step_matches_allocating_step(G):
 
 def test_noalloc_rejects_more_rows_than_the_array_holds(G):
     n = G.GS_NOALLOC_MAX_ROWS + 1
-    run = GpuRun(synth.scene_uniform(n, 882))
+    run = GpuScene(synth.scene_uniform(n, 882))
     gh = {g: torch.zeros(v.shape, dtype=torch.float32).pin_memory() for g, v in run.attrs.items()}
     with pytest.raises(G.GsError) as e:
         G.gs_step_host_noalloc(run.h, G.make_attrs(run.attrs), G.make_attrs(gh),
