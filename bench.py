@@ -429,10 +429,28 @@ def next_rows_leg(G, synth, steps, warmup=10, aiu_prob=0.1):
     torch.cuda.synchronize()
     dt = e0.elapsed_time(e1) / 1e3 / reps
     na_rows = int(cnt.item())
+    # the standalone visibility filter over the 6 M scene's means: mask,
+    # compacted visible list and count
+    wl6 = synth.WORKLOADS["c5_6m"]
+    xyz = torch.from_numpy(synth.scene_blobs(wl6.n, wl6.seed, wl6.extent)["xyz"]).cuda()
+    cam = G.make_camera(wl6.cameras()[3])
+    mask = torch.empty(n, dtype=torch.uint8, device="cuda")
+    for _ in range(3):
+        G.gs_visibility(h, xyz, cam, mask, rows, cnt)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        G.gs_visibility(h, xyz, cam, mask, rows, cnt)
+    e1.record()
+    torch.cuda.synchronize()
+    dv = e0.elapsed_time(e1) / 1e3 / reps
+    nvis = int(cnt.item())
     G.gs_opt_destroy(h)
     out["active_rows_6m"] = {"ms": dt * 1e3, "n_active": na_rows,
                              "hbm_gbs": (4 * n + 4 * na_rows) / dt / 1e9,
                              "bytes": "4 B read per logit + 4 B written per active row (algorithmic)"}
+    out["visibility_6m"] = {"ms": dv * 1e3, "n_visible": nvis, "hbm_gbs": (13 * n + 4 * nvis) / dv / 1e9,
+                            "bytes": "12 B mean read + 1 B mask written per row, 4 B per visible row (algorithmic)"}
     return out
 
 

@@ -55,6 +55,63 @@ __global__ void __launch_bounds__(kThreads) visibility_kernel(const float *__res
     }
 }
 
+// Four consecutive rows per thread, for 16-B aligned means: three float4
+// loads carry the rows' 12 values, one 32-bit store their mask bytes.  The
+// CTA's visible rows are placed by an exclusive scan of the per-thread
+// counts, so the list stays ascending within the CTA's 1024 rows.
+constexpr int kVisRpt = 4;
+
+__global__ void __launch_bounds__(kThreads) visibility4_kernel(const float *__restrict__ xyz, int32_t n,
+                                                               const gs_camera cam, uint8_t *__restrict__ mask,
+                                                               int32_t *__restrict__ list,
+                                                               unsigned long long *__restrict__ count)
+{
+    __shared__ int32_t s_warp[kThreads / 32];
+    __shared__ unsigned long long s_base;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t r0 = ((int64_t)blockIdx.x * kThreads + tid) * kVisRpt;
+    const float *c = reinterpret_cast<const float *>(&cam);
+    unsigned vis = 0;                      // bit j: row r0 + j is visible
+    if (r0 + kVisRpt <= n) {
+        const float4 *p = reinterpret_cast<const float4 *>(xyz + r0 * 3);
+        const float4 a = __ldcs(p), b = __ldcs(p + 1), d = __ldcs(p + 2);
+        vis = (frustum_visible(a.x, a.y, a.z, c) ? 1u : 0u) | (frustum_visible(a.w, b.x, b.y, c) ? 2u : 0u) |
+              (frustum_visible(b.z, b.w, d.x, c) ? 4u : 0u) | (frustum_visible(d.y, d.z, d.w, c) ? 8u : 0u);
+        __stcs(reinterpret_cast<uint32_t *>(mask + r0),
+               (vis & 1u) | ((vis >> 1) & 1u) << 8 | ((vis >> 2) & 1u) << 16 | ((vis >> 3) & 1u) << 24);
+    } else {
+        for (int j = 0; j < kVisRpt && r0 + j < n; ++j) {
+            const float *q = xyz + (r0 + j) * 3;
+            const bool v = frustum_visible(q[0], q[1], q[2], c);
+            vis |= v ? 1u << j : 0u;
+            mask[r0 + j] = v ? 1 : 0;
+        }
+    }
+    if (!count) return;
+    const int mine = __popc(vis);
+    int incl = mine;                       // inclusive scan of the counts within the warp
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (tid == 0) {
+        int tot = 0;
+        for (int q = 0; q < kThreads / 32; ++q) tot += s_warp[q];
+        s_base = tot ? atomicAdd(count, (unsigned long long)tot) : 0ull;
+    }
+    __syncthreads();
+    if (list && vis) {
+        int off = incl - mine;
+        for (int q = 0; q < warp; ++q) off += s_warp[q];
+        int32_t *dst = list + s_base + off;
+        for (int j = 0; j < kVisRpt; ++j)
+            if (vis & (1u << j)) *dst++ = (int32_t)(r0 + j);
+    }
+}
+
 // --------------------------------------------------------------- bias table
 // 1 - beta^k in FP64 for k = 0 .. len-1 (beta^k by binary exponentiation),
 // plus the FP32 factors the step consumes: 1/(1 - b1^k), 1/sqrt(1 - b2^k).
@@ -245,7 +302,6 @@ __global__ void import_f16b_kernel(const StateView st, int32_t n, const float *_
 }
 
 // ----------------------------------------------------------- attribute gather
-// One thread per (output row, canonical column).
 // A flat index space: first one thread per float4 of the 16-B aligned groups
 // (12 SH float4 and the rotation of each row), then one thread per row for
 // its seven small values (xyz, scale, opacity).  Consecutive threads write
@@ -380,7 +436,11 @@ cudaError_t launch_visibility(const float *xyz, int32_t n, const float cam[16], 
     if (n <= 0) return cudaSuccess;
     gs_camera c;
     memcpy(&c, cam, sizeof(c));
-    visibility_kernel<<<blocks_for(n), kThreads, 0, s>>>(xyz, n, c, mask, list, count);
+    if (((uintptr_t)xyz & 15u) == 0 && ((uintptr_t)mask & 3u) == 0)
+        visibility4_kernel<<<blocks_for(((int64_t)n + kVisRpt - 1) / kVisRpt), kThreads, 0, s>>>(xyz, n, c, mask,
+                                                                                                  list, count);
+    else
+        visibility_kernel<<<blocks_for(n), kThreads, 0, s>>>(xyz, n, c, mask, list, count);
     return cudaGetLastError();
 }
 

@@ -59,6 +59,50 @@ def test_visibility_bit_exact(G, orc, scene):
     run.close()
 
 
+def _runs_ascending(lst, tile):
+    """Each tile of `tile` rows forms one contiguous, ascending run of the list."""
+    ids = lst // tile
+    starts = np.flatnonzero(np.r_[True, ids[1:] != ids[:-1]])
+    assert len(np.unique(ids)) == len(starts), "a tile's rows are split across the list"
+    same = ids[1:] == ids[:-1]
+    assert np.all(lst[1:][same] > lst[:-1][same]), "rows within a tile not ascending"
+
+
+@pytest.mark.parametrize("offset", [0, 1])
+def test_visibility_layouts_and_list_order(G, orc, offset):
+    """Aligned means (four rows per thread) and means starting 12 B past a
+    16-B boundary (one row per thread) give the same mask, count and list
+    set; each CTA's share of the list is one ascending run."""
+    n = 100_003
+    groups = synth.scene_blobs(n + offset, 93, 12.5)
+    xyz_all = torch.from_numpy(groups["xyz"]).cuda()
+    xyz = xyz_all[offset:]
+    assert (xyz.data_ptr() % 16 == 0) == (offset == 0)
+    run = GpuScene({k: v[offset:] for k, v in groups.items()})
+    mask_all = torch.zeros(n + offset, dtype=torch.uint8, device="cuda")
+    mask = mask_all[offset:]
+    rows = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    for cam in synth.ring_cameras(4):
+        G.gs_visibility(run.h, xyz, G.make_camera(cam), mask, rows, cnt)
+        torch.cuda.synchronize()
+        ref = orc.visibility_f32(groups["xyz"][offset:], cam)
+        assert np.array_equal(mask.cpu().numpy(), ref)
+        c = int(cnt.item())
+        assert c == int(ref.sum())
+        lst = rows.cpu().numpy()[:c]
+        assert np.array_equal(np.sort(lst), np.nonzero(ref)[0])
+        _runs_ascending(lst, 1024 if offset == 0 else 256)
+        # mask alone, no list or count
+        mask.zero_()
+        G.gs_visibility(run.h, xyz, G.make_camera(cam), mask, None, None)
+        torch.cuda.synchronize()
+        assert np.array_equal(mask.cpu().numpy(), ref)
+    if offset:
+        assert int(mask_all[0].item()) == 0, "write before the mask's first row"
+    run.close()
+
+
 # ---------------------------------------------------------- one-step parity
 
 @pytest.mark.parametrize("scene,restate", [("uniform", False), ("blobs", True)])
