@@ -51,8 +51,8 @@ BYTES_ROW_VIS = 12          # every row: the mean read by the frustum test
 # DRAM bytes (read + write) of one step_tile launch from an ncu capture of the
 # current kernel, with the algorithmic bytes of that same launch
 # (profiles/step_tile_c2_1m.md).
-NCU_TRAFFIC = {("c2_1m", "fp32"): (541.316864e6, 476.3e6),
-               ("c2_1m", "fp16_block"): (398.551808e6, 351.2e6)}
+NCU_TRAFFIC = {("c2_1m", "fp32"): (542.184704e6, 476.3e6),
+               ("c2_1m", "fp16_block"): (398.065664e6, 351.2e6)}
 
 
 def bytes_visible(prec: str) -> int:
@@ -365,6 +365,8 @@ def run_ours(args):
                                   **legs}
     if rank == 0 and args.next_rows:
         out["next_rows"] = next_rows_leg(G, synth, args.next_steps)
+    if rank == 0 and args.ceiling:
+        out["access_ceiling"] = access_ceiling_leg(G, synth)
     if rank == 0 and args.reindex:
         out["reindex"] = reindex_leg(G, synth, args.reindex_steps)
     if rank == 0 and args.batched:
@@ -375,6 +377,61 @@ def run_ours(args):
         print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def access_ceiling_leg(G, synth, reps=320, n_views=16):
+    """The FP32 step beside gs_copy_rows on the same visible rows.  The copy
+    reads every attribute, gradient, moment and step-counter byte the step
+    reads for those rows and writes back every byte it writes (the same
+    1648 B per row), with no arithmetic, at full parallelism: the cost of
+    the scattered row accesses alone.  step_over_copy is what the update,
+    the frustum test over every row (12 B each, not in the copy) and the
+    in-kernel compaction add to it.  n_views views of each workload, cycled;
+    no RSR steps."""
+    import torch
+    out = {}
+    for wname in (WORKLOAD, MIXED_WORKLOAD):
+        wl = synth.WORKLOADS[wname]
+        sc = Scene(G, synth, wl, wl.seed, n_views)
+        h = G.gs_opt_init(G.make_config(n_pixels=wl.n_pixels), wl.n)
+        masks = torch.zeros((n_views, wl.n), dtype=torch.uint8, device="cuda")
+        lists = torch.zeros((n_views, wl.n), dtype=torch.int32, device="cuda")
+        cnts = torch.zeros(n_views, dtype=torch.int64, device="cuda")
+        for i in range(n_views):
+            G.gs_visibility(h, sc.attrs["xyz"], sc.CAMS[sc.order[i]], masks[i], lists[i], cnts[i:i + 1])
+        nvs = cnts.cpu().tolist()
+        P = [G.make_params(synth.lr_for_step(k, 1000), k, dar_opacity=wl.dar, dar_scale=wl.dar)
+             for k in range(1, n_views + 1)]
+        ng = len(sc.GB)
+
+        def timed(launch):
+            for i in range(3 * n_views):
+                launch(i % n_views)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for i in range(reps):
+                launch(i % n_views)
+            e1.record()
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps
+
+        copy_ms = timed(lambda i: G.gs_copy_rows(h, sc.A, sc.GB[i % ng], lists[i], nvs[i]))
+        mask_ms = timed(lambda i: G.gs_step(h, sc.A, sc.GB[i % ng], masks[i], P[i]))
+        cam_ms = timed(lambda i: G.gs_step_camera(h, sc.A, sc.GB[i % ng], sc.CAMS[sc.order[i]], P[i]))
+        G.gs_opt_destroy(h)
+        nv = sum(nvs[i % n_views] for i in range(reps)) / reps
+        row_bytes = 3 * 236 + STATE_RW["fp32"] + T_RW["fp32"] + 4       # + the list entry
+        out[wname] = {"visible_rows_mean": nv, "copy_rows_ms": copy_ms,
+                      "copy_rows_gbs": nv * row_bytes / copy_ms / 1e6,
+                      "copy_rows_frac": nv * row_bytes / copy_ms / 1e6 / _peaks()[0],
+                      "step_mask_ms": mask_ms, "step_camera_ms": cam_ms,
+                      "step_over_copy": cam_ms / copy_ms}
+        del sc, masks, lists
+        torch.cuda.empty_cache()
+    out["bytes"] = ("copy: 1664 B per listed row (attributes and moments read and written, gradients read, "
+                    "t read and written, the list entry read)")
+    return out
 
 
 def next_rows_leg(G, synth, steps, warmup=10, aiu_prob=0.1):
@@ -760,6 +817,7 @@ def main():
     ap.add_argument("--no-batched", dest="batched", action="store_false")
     ap.add_argument("--no-reindex", dest="reindex", action="store_false")
     ap.add_argument("--no-next-rows", dest="next_rows", action="store_false")
+    ap.add_argument("--no-ceiling", dest="ceiling", action="store_false")
     ap.add_argument("--density-sweep", action="store_true",
                     help="only time the plain step at several visible densities (random-row masks)")
     ap.add_argument("--next-steps", type=int, default=300)

@@ -431,6 +431,22 @@ gs_status gs_opt_import_state(gs_opt *opt, const float *m, const float *v, const
  */
 gs_status gs_active_rows(gs_opt *opt, const float *opacity, int32_t *rows, int64_t *n_active, void *stream);
 
+/*
+ * Diagnostic: the memory traffic of one step over the listed rows, without
+ * the update.  For each listed row, every attribute, gradient, moment and
+ * step-counter byte that gs_step reads for a visible row is read, and every
+ * byte it writes is written back with the value just read, so nothing
+ * changes.  Its time beside gs_step's on the same rows separates what the
+ * scattered row accesses cost from what the update adds.
+ *   attrs, grads  as for gs_step (device buffers of the context's n_rows).
+ *   rows          device [n_listed] int32, each in [0, n_rows), e.g.
+ *                 gs_visibility's visible_rows; 0 <= n_listed <= n_rows.
+ * An out-of-range row is skipped and recorded as for gs_reindex_state.  One
+ * launch; no allocation.
+ */
+gs_status gs_copy_rows(gs_opt *opt, const gs_attrs *attrs, const gs_grads *grads, const int32_t *rows,
+                       int64_t n_listed, void *stream);
+
 /* Length of the context's bias-correction table: the first step count k at
  * which both FP32 factors 1/(1 - beta1^k) and 1/sqrt(1 - beta2^k) round to
  * exactly 1 (15 936 for beta2 = 0.999), at most 2^22.  -1 for NULL. */

@@ -579,6 +579,22 @@ gs_status gs_gather_attrs(gs_opt *o, const gs_attrs *in, int64_t n_in, const gs_
                                                 static_cast<cudaStream_t>(stream)));
 }
 
+gs_status gs_copy_rows(gs_opt *o, const gs_attrs *attrs, const gs_grads *grads, const int32_t *rows,
+                       int64_t n_listed, void *stream)
+{
+    gs_status st = precheck(o);
+    if (st != GS_OK) return st;
+    const int64_t n = o->n_rows;
+    if (!attrs || !grads || n_listed < 0 || n_listed > n) return GS_ERR_INVALID_ARG;
+    if (!attrs_ok(o, *attrs, n) || !attrs_ok(o, *grads, n) || !dev_ok(o, rows, 4 * (size_t)n_listed, 4) ||
+        (n_listed && !rows))
+        return GS_ERR_INVALID_ARG;
+    const int32_t row_bytes = (int32_t)state_row_bytes(o->cfg.prec);
+    const int32_t used = o->cfg.prec == GS_MOM_FP32 ? 240 : row_bytes;    // FP32: 59 values + t
+    return fail_cuda(o, gs::launch_copy_rows(*attrs, *grads, o->m, o->v, row_bytes, used, rows, n_listed,
+                                             (int32_t)n, o->err, static_cast<cudaStream_t>(stream)));
+}
+
 gs_status gs_active_rows(gs_opt *o, const float *opacity, int32_t *rows, int64_t *n_active, void *stream)
 {
     gs_status st = precheck(o);

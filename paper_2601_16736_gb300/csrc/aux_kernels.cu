@@ -343,6 +343,83 @@ __global__ void gather_attrs_kernel(const gs_attrs in, int32_t n_in, const gs_at
     }
 }
 
+// ------------------------------------------------------------- row copy
+// The memory traffic of a step over listed rows, without the update: each
+// byte a visible row's step reads is read, each byte it writes is written
+// back with the value read.  Gradient loads are volatile so they are issued
+// although their values are unused.  Items are kind-major (SH chunks, then
+// moment-row chunks, then the four small groups) so warps stay convergent.
+struct CopyRowsArgs {
+    gs_attrs a;
+    gs_grads g;
+    char *m, *v;
+    int32_t row_bytes, chunks;              // state row stride; 16-B chunks used per row
+    const int32_t *rows;
+    int64_t nl;
+    int32_t n;
+    int32_t *err;
+};
+
+__device__ __forceinline__ void touch4(const float *p)
+{
+    float x, y, z, w;
+    asm volatile("ld.global.cs.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(x), "=f"(y), "=f"(z), "=f"(w) : "l"(p));
+}
+
+__device__ __forceinline__ void touch1(const float *p)
+{
+    float x;
+    asm volatile("ld.global.cs.f32 %0, [%1];" : "=f"(x) : "l"(p));
+}
+
+__global__ void __launch_bounds__(kThreads) copy_rows_kernel(const CopyRowsArgs c)
+{
+    const int64_t nl = c.nl, e_sh = 12 * nl, e_m = e_sh + (int64_t)c.chunks * nl, e_st = e_m + (int64_t)c.chunks * nl;
+    const int64_t total = e_st + 4 * nl;
+    for (int64_t w = (int64_t)blockIdx.x * kThreads + threadIdx.x; w < total; w += (int64_t)gridDim.x * kThreads) {
+        int64_t j;
+        int i;
+        if (w < e_sh) {
+            j = w / 12;
+            i = (int)(w - 12 * j);
+        } else if (w < e_st) {
+            const int64_t q = w < e_m ? w - e_sh : w - e_m;   // m rows, then v rows, chunks of a row adjacent
+            j = q / c.chunks;
+            i = (int)(q - j * c.chunks);
+        } else {
+            const int64_t q = w - e_st;
+            i = (int)(q / nl);                   // 0 xyz, 1 rot, 2 scale, 3 opacity
+            j = q - (int64_t)i * nl;
+        }
+        const int32_t r32 = c.rows[j];
+        if (r32 < 0 || r32 >= c.n) {
+            if (w < e_sh && i == 0) record_error(c.err, GS_ERR_INVALID_ARG);
+            continue;
+        }
+        const int64_t r = r32;
+        if (w < e_sh) {
+            float4 *t = reinterpret_cast<float4 *>(c.a.sh + r * 48) + i;
+            touch4(c.g.sh + r * 48 + 4 * i);
+            __stcs(t, *t);
+        } else if (w < e_st) {
+            uint4 *t = reinterpret_cast<uint4 *>((w < e_m ? c.m : c.v) + r * c.row_bytes) + i;
+            __stcs(t, *t);
+        } else if (i == 1) {
+            float4 *t = reinterpret_cast<float4 *>(c.a.rot + r * 4);
+            touch4(c.g.rot + r * 4);
+            __stcs(t, *t);
+        } else {
+            float *t = i == 0 ? c.a.xyz + r * 3 : i == 2 ? c.a.scale + r * 3 : c.a.opacity + r;
+            const float *g = i == 0 ? c.g.xyz + r * 3 : i == 2 ? c.g.scale + r * 3 : c.g.opacity + r;
+            const int k = i == 3 ? 1 : 3;
+            for (int u = 0; u < k; ++u) {
+                touch1(g + u);
+                __stcs(t + u, t[u]);
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------ active rows
 // The ascending list of rows with tau > tau_act (opacity > 1/255) in three
 // passes: per-block counts of kActRows rows, one CTA turning them into
@@ -505,6 +582,23 @@ cudaError_t launch_gather_attrs(const gs_attrs &in, int32_t n_in, const gs_attrs
 {
     if (n_new <= 0) return cudaSuccess;
     gather_attrs_kernel<<<blocks_for((int64_t)n_new * (kGatherVec + 1)), kThreads, 0, s>>>(in, n_in, out, src, n_new, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_rows(const gs_attrs &a, const gs_grads &g, void *m, void *v, int32_t row_bytes,
+                             int32_t used_bytes, const int32_t *rows, int64_t n_listed, int32_t n, int32_t *err,
+                             cudaStream_t s)
+{
+    if (n_listed <= 0) return cudaSuccess;
+    CopyRowsArgs c{a, g, static_cast<char *>(m), static_cast<char *>(v), row_bytes, used_bytes / 16, rows, n_listed,
+                   n, err};
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int64_t items = (16 + 2 * (int64_t)c.chunks) * n_listed;
+    const unsigned grid = (unsigned)std::min<int64_t>((items + kThreads - 1) / kThreads, 8 * (int64_t)sms);
+    copy_rows_kernel<<<grid, kThreads, 0, s>>>(c);
     return cudaGetLastError();
 }
 

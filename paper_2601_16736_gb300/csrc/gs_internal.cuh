@@ -90,6 +90,7 @@ struct StepArgs {
     uint64_t aiu_thr;            // AIU-sampled iff (draw >> 11) < aiu_thr
     unsigned long long *n_active;   // optional, accumulated with atomicAdd
     int32_t g_host;              // gradients are pinned host memory read in place
+    int32_t tile_ahead;          // CTAs resident at once (0: no look-ahead prefetch)
 };
 
 // ------------------------------------------------------- device helpers
@@ -242,6 +243,9 @@ cudaError_t launch_export(const StateView &st, int32_t n, float *m_out, float *v
                           cudaStream_t s);
 cudaError_t launch_import(const StateView &st, int32_t n, const float *m_in, const float *v_in,
                           const uint32_t *t_in, cudaStream_t s);
+cudaError_t launch_copy_rows(const gs_attrs &a, const gs_grads &g, void *m, void *v, int32_t row_bytes,
+                             int32_t used_bytes, const int32_t *rows, int64_t n_listed, int32_t n, int32_t *err,
+                             cudaStream_t s);
 cudaError_t launch_gather_attrs(const gs_attrs &in, int32_t n_in, const gs_attrs &out,
                                 const int32_t *src, int32_t n_new, int32_t *err, cudaStream_t s);
 

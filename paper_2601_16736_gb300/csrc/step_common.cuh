@@ -519,6 +519,43 @@ __device__ __forceinline__ void prefetch_row_l2(const StepArgs &a, int32_t row)
                  "n"(kRowBytes) : "memory");
 }
 
+// Ask L2 for the visibility inputs (means or mask bytes) of the tile one wave
+// of resident CTAs ahead: the tile that starts when a slot frees, whose
+// phase A then finds them on chip instead of waiting a DRAM round trip.  A
+// hint only; nothing waits for it.  Whole tiles only, 16-B aligned sources.
+template <int kTile>
+__device__ __forceinline__ void prefetch_tile_ahead(const StepArgs &a, const int vis_src)
+{
+    static_assert((kTile * 12) % 16 == 0 && kTile % 16 == 0, "bulk prefetch sizes are multiples of 16 B");
+    if (threadIdx.x != 0 || a.tile_ahead <= 0) return;
+    const int64_t q = ((int64_t)blockIdx.x + a.tile_ahead) * kTile;
+    if (q + kTile > (int64_t)a.n_rows) return;
+    if (vis_src == kVisCamera && ((uintptr_t)a.a_xyz & 15u) == 0)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.a_xyz + q * 3), "n"(kTile * 12) : "memory");
+    else if (vis_src == kVisMask && ((uintptr_t)a.mask_in & 15u) == 0)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.mask_in + q), "n"(kTile) : "memory");
+}
+
+// CTAs of kernel `fn` (kThreads threads, static shared memory only) resident
+// at once on the current device, cached per device in `cache`; 0 if the
+// query fails (the caller then launches without the look-ahead).
+inline int resident_ctas(const void *fn, int *cache)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    int &c = cache[dev & 63];
+    if (!c) {
+        int per_sm = 0, sms = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, 0) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        c = per_sm * sms;
+    }
+    return c;
+}
+
 // Prefetch when at most 60 % of the tile's rows are visible.
 template <int kTile>
 __device__ __forceinline__ bool sparse_tile(int nv) { return 5 * nv <= 3 * kTile; }

@@ -445,6 +445,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) step_tile_x(const StepAr
     using S = State<kPrec>;
     constexpr int kNsh = 48 / kW;
     __shared__ TileListsX<kTile> L;
+    prefetch_tile_ahead<kTile>(a, vis_src);
     const int64_t r0 = (int64_t)blockIdx.x * kTile;
     int nv, ni;
     tile_decide_x<kTile, S::kRowBytes, S::kTByte>(a, vis_src, r0, L, nv, ni);
@@ -485,27 +486,32 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) step_tile_x(const StepAr
 constexpr int kExtTile = 256;
 constexpr int kExtMinBlocks = 4;
 
+namespace {
+
+template <int kPrec, int kW>
+cudaError_t launch_ext_t(const StepArgs &a, int vis_src, cudaStream_t s)
+{
+    auto k = step_tile_x<kExtTile, kExtMinBlocks, kPrec, kW>;
+    static int s_res[64] = {};
+    StepArgs b = a;
+    b.tile_ahead = resident_ctas(reinterpret_cast<const void *>(k), s_res);
+    const unsigned grid = (unsigned)((a.n_rows + kExtTile - 1) / kExtTile);
+    k<<<grid, kThreads, 0, s>>>(b, vis_src);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
 cudaError_t launch_step_ext(const StepArgs &a, int prec, int vis_src, cudaStream_t s)
 {
     if (a.n_rows <= 0) return cudaSuccess;
-    const unsigned grid = (unsigned)((a.n_rows + kExtTile - 1) / kExtTile);
     switch (prec) {
-    case GS_MOM_FP32:
-        step_tile_x<kExtTile, kExtMinBlocks, GS_MOM_FP32, 4><<<grid, kThreads, 0, s>>>(a, vis_src);
-        break;
-    case GS_MOM_BF16:
-        step_tile_x<kExtTile, kExtMinBlocks, GS_MOM_BF16, 8><<<grid, kThreads, 0, s>>>(a, vis_src);
-        break;
-    case GS_MOM_BF16_HYBRID:
-        step_tile_x<kExtTile, kExtMinBlocks, GS_MOM_BF16_HYBRID, 8><<<grid, kThreads, 0, s>>>(a, vis_src);
-        break;
-    case GS_MOM_FP16_BLOCK:
-        step_tile_x<kExtTile, kExtMinBlocks, GS_MOM_FP16_BLOCK, 8><<<grid, kThreads, 0, s>>>(a, vis_src);
-        break;
-    default:
-        return cudaErrorNotSupported;
+    case GS_MOM_FP32: return launch_ext_t<GS_MOM_FP32, 4>(a, vis_src, s);
+    case GS_MOM_BF16: return launch_ext_t<GS_MOM_BF16, 8>(a, vis_src, s);
+    case GS_MOM_BF16_HYBRID: return launch_ext_t<GS_MOM_BF16_HYBRID, 8>(a, vis_src, s);
+    case GS_MOM_FP16_BLOCK: return launch_ext_t<GS_MOM_FP16_BLOCK, 8>(a, vis_src, s);
+    default: return cudaErrorNotSupported;
     }
-    return cudaGetLastError();
 }
 
 }  // namespace gs

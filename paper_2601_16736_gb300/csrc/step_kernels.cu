@@ -160,6 +160,7 @@ template <int kTile, int kMinBlocks, int kPrec, int kW>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) step_tile(const StepArgs a, const int vis_src)
 {
     __shared__ TileLists<kTile> L;
+    prefetch_tile_ahead<kTile>(a, vis_src);
     process_tile<kTile, kPrec, kW>(a, vis_src, (int64_t)blockIdx.x * kTile, L);
 }
 
@@ -218,8 +219,12 @@ namespace {
 template <int kPrec, int kW>
 cudaError_t launch_tiles(const StepArgs &a, int vis_src, cudaStream_t s)
 {
+    auto k = step_tile<kStepTile, kStepMinBlocks, kPrec, kW>;
+    static int s_res[64] = {};
+    StepArgs b = a;
+    b.tile_ahead = resident_ctas(reinterpret_cast<const void *>(k), s_res);
     const unsigned n_tiles = (unsigned)((a.n_rows + kStepTile - 1) / kStepTile);
-    step_tile<kStepTile, kStepMinBlocks, kPrec, kW><<<n_tiles, kThreads, 0, s>>>(a, vis_src);
+    k<<<n_tiles, kThreads, 0, s>>>(b, vis_src);
     return cudaGetLastError();
 }
 

@@ -87,6 +87,7 @@ def _load():
         "gs_reindex_state": ([P, P, P, i64, P], ctypes.c_int),
         "gs_gather_attrs": ([P, ctypes.POINTER(gs_attrs), i64, ctypes.POINTER(gs_attrs), P, i64, P], ctypes.c_int),
         "gs_active_rows": ([P, P, P, P, P], ctypes.c_int),
+        "gs_copy_rows": ([P, ctypes.POINTER(gs_attrs), ctypes.POINTER(gs_attrs), P, i64, P], ctypes.c_int),
         "gs_opt_export_state": ([P, P, P, P, P], ctypes.c_int),
         "gs_opt_import_state": ([P, P, P, P, P], ctypes.c_int),
         "gs_bias_table_len": ([P], i64),
@@ -195,6 +196,11 @@ def gs_opt_rows(h) -> int:
 def gs_visibility(h, xyz, cam: gs_camera, mask, visible_rows=None, n_visible=None, stream=None) -> None:
     _check(_load().gs_visibility(h, _ptr(xyz), ctypes.byref(cam), _ptr(mask), _ptr(visible_rows), _ptr(n_visible),
                                  _stream(stream)), "gs_visibility")
+
+
+def gs_copy_rows(h, attrs: gs_attrs, grads: gs_attrs, rows, n_listed: int, stream=None) -> None:
+    _check(_load().gs_copy_rows(h, ctypes.byref(attrs), ctypes.byref(grads), _ptr(rows), n_listed, _stream(stream)),
+           "gs_copy_rows")
 
 
 def gs_step(h, attrs: gs_attrs, grads: gs_attrs, mask, params: gs_step_params, stream=None) -> None:
