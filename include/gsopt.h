@@ -425,9 +425,10 @@ gs_status gs_opt_import_state(gs_opt *opt, const float *m, const float *v, const
  *   opacity  device [n_rows] float32 logits tau, read-only.
  *   rows     device [n_rows] int32 out, optional (NULL: count only).
  *   n_active device int64 out (overwritten), required.
- * Three launches (per-block counts, a scan over the blocks, the ordered
- * write); a scratch array of one int32 per 1024 rows is kept by the context
- * (allocated synchronously on first use or growth).
+ * Two launches (per-block counts; the ordered write, where each block adds
+ * up the counts of the blocks before it); a scratch array of one int32 per
+ * 4096 rows is kept by the context (allocated synchronously on first use or
+ * growth).
  */
 gs_status gs_active_rows(gs_opt *opt, const float *opacity, int32_t *rows, int64_t *n_active, void *stream);
 

@@ -421,86 +421,100 @@ __global__ void __launch_bounds__(kThreads) copy_rows_kernel(const CopyRowsArgs 
 }
 
 // ------------------------------------------------------------ active rows
-// The ascending list of rows with tau > tau_act (opacity > 1/255) in three
-// passes: per-block counts of kActRows rows, one CTA turning them into
-// offsets (exclusive scan, carried across chunks of kThreads blocks) plus the
-// total, and the ordered write (warp ballots, then warps and row groups in
-// row order).
-constexpr int kActRpt = 4;
+// The ascending list of rows with tau > tau_act (opacity > 1/255) in two
+// passes over blocks of kActRows rows: per-block counts, then the ordered
+// write.  In the second pass every block adds up the counts of the blocks
+// before it (a few thousand ints, read from L2) to find its offset, so no
+// separate scan is needed; the last block also writes the total.  Rows of a
+// block are taken as kActRpt strided passes of the CTA (coalesced loads, all
+// in flight at once), which is also their ascending order.
+constexpr int kActRpt = 16;
 constexpr int kActRows = kThreads * kActRpt;
+constexpr int kActWarps = kThreads / 32;
 
-__global__ void active_count_kernel(const float *__restrict__ tau, int32_t n, float tau_act, int32_t *blk)
+__global__ void __launch_bounds__(kThreads) active_count_kernel(const float *__restrict__ tau, int32_t n,
+                                                                float tau_act, int32_t *__restrict__ blk)
 {
-    __shared__ int32_t warp_sum[kThreads / 32];
+    __shared__ int32_t warp_sum[kActWarps];
     const int64_t r0 = (int64_t)blockIdx.x * kActRows;
-    int c = 0;
+    float x[kActRpt];
 #pragma unroll
     for (int j = 0; j < kActRpt; ++j) {
         const int64_t r = r0 + j * kThreads + threadIdx.x;
-        c += (r < n && __ldcs(tau + r) > tau_act) ? 1 : 0;
+        x[j] = r < n ? __ldg(tau + r) : -INFINITY;      // kept in L2 for the write pass
     }
+    int c = 0;
+#pragma unroll
+    for (int j = 0; j < kActRpt; ++j) c += x[j] > tau_act ? 1 : 0;
     c = __reduce_add_sync(0xffffffffu, c);
     if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = c;
     __syncthreads();
     if (threadIdx.x == 0) {
         int s = 0;
-        for (int w = 0; w < kThreads / 32; ++w) s += warp_sum[w];
+        for (int w = 0; w < kActWarps; ++w) s += warp_sum[w];
         blk[blockIdx.x] = s;
     }
 }
 
-__global__ void active_scan_kernel(int32_t *blk, int32_t nblk, long long *total)
+// rows == NULL: count only (only the last block runs, to write the total).
+__global__ void __launch_bounds__(kThreads) active_write_kernel(const float *__restrict__ tau, int32_t n,
+                                                                float tau_act, const int32_t *__restrict__ blk,
+                                                                int32_t *__restrict__ rows, long long *total)
 {
-    __shared__ int32_t warp_sum[kThreads / 32];
-    __shared__ int32_t carry;
+    __shared__ int32_t cnt[kActRpt * kActWarps];      // per (pass, warp), then its exclusive offset
+    __shared__ int32_t part[kActWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) carry = 0;
+    const bool last = blockIdx.x == gridDim.x - 1;
+    if (!rows && !last) return;
+    const int64_t r0 = (int64_t)blockIdx.x * kActRows;
+    float x[kActRpt];
+#pragma unroll
+    for (int j = 0; j < kActRpt; ++j) {
+        const int64_t r = r0 + j * kThreads + threadIdx.x;
+        x[j] = r < n ? __ldcs(tau + r) : -INFINITY;
+    }
+    int before = 0;                                      // counts of the blocks before this one
+    for (int b = threadIdx.x; b < (int)blockIdx.x; b += kThreads) before += blk[b];
+    before = __reduce_add_sync(0xffffffffu, before);
+    unsigned bal[kActRpt];
+#pragma unroll
+    for (int j = 0; j < kActRpt; ++j) {
+        bal[j] = __ballot_sync(0xffffffffu, x[j] > tau_act);
+        if (lane == 0) cnt[j * kActWarps + warp] = __popc(bal[j]);
+    }
+    if (lane == 0) part[warp] = before;
     __syncthreads();
-    for (int base = 0; base < nblk; base += kThreads) {
-        const int i = base + threadIdx.x;
-        const int x = i < nblk ? blk[i] : 0;
-        int incl = x;                                   // inclusive scan within the warp
+    if (warp == 0) {                                     // exclusive scan of the kActRpt*kActWarps counts
+        constexpr int kPer = kActRpt * kActWarps / 32;
+        int v[kPer], sum = 0;
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            v[q] = cnt[lane * kPer + q];
+            sum += v[q];
+        }
+        int incl = sum;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, incl, d);
             if (lane >= d) incl += y;
         }
-        if (lane == 31) warp_sum[warp] = incl;
-        __syncthreads();
-        int before = carry;
-        for (int w = 0; w < warp; ++w) before += warp_sum[w];
-        if (i < nblk) blk[i] = before + incl - x;       // exclusive offset of block i
-        __syncthreads();
-        if (threadIdx.x == kThreads - 1) carry = before + incl;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *total = carry;
-}
-
-__global__ void active_write_kernel(const float *__restrict__ tau, int32_t n, float tau_act,
-                                    const int32_t *__restrict__ off, int32_t *__restrict__ rows)
-{
-    constexpr int kWarps = kThreads / 32;
-    __shared__ int32_t cnt[kActRpt * kWarps];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t r0 = (int64_t)blockIdx.x * kActRows;
-    unsigned bal[kActRpt];
+        int base = 0;
+        for (int w = 0; w < kActWarps; ++w) base += part[w];
+        int run = base + incl - sum;
 #pragma unroll
-    for (int j = 0; j < kActRpt; ++j) {
-        const int64_t r = r0 + j * kThreads + threadIdx.x;
-        bal[j] = __ballot_sync(0xffffffffu, r < n && tau[r] > tau_act);
-        if (lane == 0) cnt[j * kWarps + warp] = __popc(bal[j]);
+        for (int q = 0; q < kPer; ++q) {
+            cnt[lane * kPer + q] = run;
+            run += v[q];
+        }
+        if (last && lane == 31 && total) *total = run;
     }
     __syncthreads();
+    if (!rows) return;
     const unsigned lt = (1u << lane) - 1u;
-    int base = off[blockIdx.x];
 #pragma unroll
-    for (int j = 0; j < kActRpt; ++j) {
-        const int me = j * kWarps + warp;
-        int b = base;
-        for (int q = 0; q < me; ++q) b += cnt[q];
-        if (bal[j] & (1u << lane)) rows[b + __popc(bal[j] & lt)] = (int32_t)(r0 + j * kThreads + threadIdx.x);
-    }
+    for (int j = 0; j < kActRpt; ++j)
+        if (bal[j] & (1u << lane))
+            rows[cnt[j * kActWarps + warp] + __popc(bal[j] & lt)] = (int32_t)(r0 + j * kThreads + threadIdx.x);
 }
 
 unsigned blocks_for(int64_t n_threads) { return (unsigned)((n_threads + kThreads - 1) / kThreads); }
@@ -610,8 +624,7 @@ cudaError_t launch_active_rows(const float *tau, int32_t n, float tau_act, int32
     if (n <= 0) return cudaMemsetAsync(n_active, 0, sizeof(long long), s);
     const int32_t nblk = (int32_t)((n + kActRows - 1) / kActRows);
     active_count_kernel<<<nblk, kThreads, 0, s>>>(tau, n, tau_act, blk);
-    active_scan_kernel<<<1, kThreads, 0, s>>>(blk, nblk, n_active);
-    if (rows) active_write_kernel<<<nblk, kThreads, 0, s>>>(tau, n, tau_act, blk, rows);
+    active_write_kernel<<<nblk, kThreads, 0, s>>>(tau, n, tau_act, blk, rows, n_active);
     return cudaGetLastError();
 }
 

@@ -183,7 +183,7 @@ def test_active_count_all_paths(G, orc):
     run.close()
 
 
-@pytest.mark.parametrize("n", [0, 1, 1023, 1024, 1025, 300_001])
+@pytest.mark.parametrize("n", [0, 1, 1023, 1024, 1025, 4095, 4096, 4097, 300_001, 2_000_003])
 def test_active_rows_matches_oracle(G, orc, n):
     rng = np.random.default_rng(1950 + n)
     tau = rng.normal(-5.5, 1.0, n).astype(np.float32)
