@@ -484,14 +484,17 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) step_tile_x(const StepAr
 }  // namespace
 
 constexpr int kExtTile = 256;
-constexpr int kExtMinBlocks = 4;
+// Resident CTAs per SM: 5 for FP32 moments (48 registers, no spills), 4 for
+// the other formats (5 would spill).
+template <int kPrec>
+constexpr int kExtMinBlocks = kPrec == GS_MOM_FP32 ? 5 : 4;
 
 namespace {
 
 template <int kPrec, int kW>
 cudaError_t launch_ext_t(const StepArgs &a, int vis_src, cudaStream_t s)
 {
-    auto k = step_tile_x<kExtTile, kExtMinBlocks, kPrec, kW>;
+    auto k = step_tile_x<kExtTile, kExtMinBlocks<kPrec>, kPrec, kW>;
     static int s_res[64] = {};
     StepArgs b = a;
     b.tile_ahead = resident_ctas(reinterpret_cast<const void *>(k), s_res);
