@@ -51,8 +51,8 @@ BYTES_ROW_VIS = 12          # every row: the mean read by the frustum test
 # DRAM bytes (read + write) of one step_tile launch from an ncu capture of the
 # current kernel, with the algorithmic bytes of that same launch
 # (profiles/step_tile_c2_1m.md).
-NCU_TRAFFIC = {("c2_1m", "fp32"): (545.419264e6, 476.3e6),
-               ("c2_1m", "fp16_block"): (398.065664e6, 351.2e6)}
+NCU_TRAFFIC = {("c2_1m", "fp32"): (545.266944e6, 476.3e6),
+               ("c2_1m", "fp16_block"): (397.612544e6, 351.2e6)}
 
 
 def bytes_visible(prec: str) -> int:
