@@ -44,9 +44,10 @@ MIXED_WORKLOAD = "c3_3m"
 # minus the row's 12-B mean, whose read is already counted by the frustum test.
 # FP32 moments 4 * 236 B; hybrid 4 * (45 * 2 + 14 * 4) B; BF16 4 * 59 * 2 B.
 # FP16-block: 4 * (59 FP16 values + 8 group exponent bytes); its t is a uint16.
-STATE_RW = {"fp32": 4 * 236, "bf16_hybrid": 4 * (45 * 2 + 14 * 4), "bf16": 4 * 118, "fp16_block": 4 * (118 + 8)}
-T_RW = {"fp32": 8, "bf16_hybrid": 8, "bf16": 8, "fp16_block": 4}
-PREC_ENUM = {"fp32": 0, "bf16": 1, "bf16_hybrid": 3, "fp16_block": 4}
+STATE_RW = {"fp32": 4 * 236, "bf16_hybrid": 4 * (45 * 2 + 14 * 4), "bf16": 4 * 118, "fp16_block": 4 * (118 + 8),
+            "fp8_e4m3": 4 * 59}
+T_RW = {"fp32": 8, "bf16_hybrid": 8, "bf16": 8, "fp16_block": 4, "fp8_e4m3": 8}
+PREC_ENUM = {"fp32": 0, "bf16": 1, "fp8_e4m3": 2, "bf16_hybrid": 3, "fp16_block": 4}
 BYTES_ROW_VIS = 12          # every row: the mean read by the frustum test
 # DRAM bytes (read + write) of one step_tile launch from an ncu capture of the
 # current kernel, with the algorithmic bytes of that same launch
@@ -351,15 +352,18 @@ def run_ours(args):
         mwl = synth.WORKLOADS[MIXED_WORKLOAD]
         msc = Scene(G, synth, mwl, mwl.seed, max(1000, args.mixed_steps + 10))
         legs = {}
-        for prec in ("fp32", "fp16_block", "bf16_hybrid", "bf16"):
+        for prec in ("fp32", "fp16_block", "bf16_hybrid", "bf16", "fp8_e4m3"):
             rr = timed_run(G, msc, prec, args.mixed_steps, 10)
             legs[prec] = {"value": rr["nv"] / rr["elapsed"], "hbm_gbs": rr["bytes_per_launch"] / rr["kern"] / 1e9,
                           "ms_per_step": rr["elapsed"] / args.mixed_steps * 1e3,
                           "bytes_per_launch": rr["bytes_per_launch"]}
             if args.mixed_error and prec != "fp32":
                 legs[prec]["error"] = error_vs_fp32(G, msc, prec)
-        for prec in ("fp16_block", "bf16_hybrid", "bf16"):
+        for prec in ("fp16_block", "bf16_hybrid", "bf16", "fp8_e4m3"):
             legs[prec]["speedup_vs_fp32"] = legs[prec]["value"] / legs["fp32"]["value"]
+        legs["fp8_e4m3"]["bytes"] = ("algorithmic: 59 B per moment per visible row; the kernel also reads the "
+                                     "64-B code rows of every invisible row (its block's scale depends on them) and "
+                                     "rewrites a block's rows when a column scale moves")
         out["mixed_precision"] = {"workload": f"{mwl.name}: {mwl.n} Gaussians, ~20% visible, {args.mixed_steps} "
                                               f"timed steps per format", "gate": "group relative L2 vs the FP32 step <= 1e-3",
                                   **legs}

@@ -54,7 +54,21 @@ size_t state_row_bytes(int prec)
     return prec == GS_MOM_FP32 ? gs::kRowBytesF32
            : prec == GS_MOM_BF16 ? gs::kRowBytesBf16
            : prec == GS_MOM_FP16_BLOCK ? gs::kRowBytesF16B
+           : prec == GS_MOM_FP8E4M3 ? gs::kRowBytesF8
                                    : gs::kRowBytesHyb;
+}
+
+// Bytes of one moment's state for `rows` rows: the rows, and for FP8 the
+// block scales after them (64 floats per 256 rows, from a 256-B boundary).
+size_t fp8_scale_offset(int64_t rows) { return ((size_t)rows * gs::kRowBytesF8 + 255) / 256 * 256; }
+size_t state_bytes(int prec, int64_t rows)
+{
+    if (prec != GS_MOM_FP8E4M3) return state_row_bytes(prec) * (size_t)rows;
+    return fp8_scale_offset(rows) + (size_t)((rows + gs::kF8BlockRows - 1) / gs::kF8BlockRows) * 64 * sizeof(float);
+}
+float *fp8_scales(void *base, int64_t capacity)
+{
+    return reinterpret_cast<float *>(static_cast<char *>(base) + fp8_scale_offset(capacity));
 }
 
 gs_status fail_cuda(gs_opt *o, cudaError_t e)
@@ -178,7 +192,7 @@ int32_t table_length(double b1, double b2)
 // allocated.
 gs_status alloc_state(gs_opt *o, int64_t rows, void **m, void **v)
 {
-    const size_t bytes = state_row_bytes(o->cfg.prec) * (size_t)(rows > 0 ? rows : 1);
+    const size_t bytes = state_bytes(o->cfg.prec, rows > 0 ? rows : 1);
     *m = *v = nullptr;
     if (cudaMalloc(m, bytes) != cudaSuccess || cudaMalloc(v, bytes) != cudaSuccess) {
         cudaGetLastError();
@@ -190,7 +204,22 @@ gs_status alloc_state(gs_opt *o, int64_t rows, void **m, void **v)
     return GS_OK;
 }
 
-gs::StateView view(const gs_opt *o) { return gs::StateView{o->cfg.prec, o->m, o->v}; }
+gs::StateView view_of(const gs_opt *o, void *m, void *v, int64_t capacity)
+{
+    gs::StateView st{o->cfg.prec, m, v};
+    if (o->cfg.prec == GS_MOM_FP8E4M3) {
+        st.msc = fp8_scales(m, capacity);
+        st.vsc = fp8_scales(v, capacity);
+    }
+    return st;
+}
+gs::StateView view(const gs_opt *o) { return view_of(o, o->m, o->v, o->capacity); }
+
+// The optional terms of the extended step are not built for FP8 moments.
+bool terms_unsupported(const gs_opt *o, const gs_step_params *p)
+{
+    return o->cfg.prec == GS_MOM_FP8E4M3 && (p->noise || p->aiu || p->n_active);
+}
 
 bool params_ok(gs_opt *o, const gs_step_params *p)
 {
@@ -224,6 +253,10 @@ void fill_args(const gs_opt *o, const gs_step_params *p, StepArgs *a)
     memset(a, 0, sizeof(*a));
     a->m = o->m;
     a->v = o->v;
+    if (o->cfg.prec == GS_MOM_FP8E4M3) {
+        a->msc = fp8_scales(o->m, o->capacity);
+        a->vsc = fp8_scales(o->v, o->capacity);
+    }
     a->fac = o->fac;
     a->fac_len = o->tab_len;
     a->n_rows = (int32_t)o->n_rows;
@@ -324,7 +357,6 @@ gs_status gs_opt_init(gs_opt **out, const gs_opt_config *cfg, int64_t n_rows, vo
     if (c.bias_mode != 0 && c.bias_mode != 1) return GS_ERR_INVALID_ARG;
     if (c.reg_mode < GS_REG_DAR || c.reg_mode > GS_REG_ADAMW_CLIP || c.reserved != 0) return GS_ERR_INVALID_ARG;
     if (c.reg_mode == GS_REG_DAR && c.n_pixels <= 0) return GS_ERR_INVALID_ARG;
-    if (c.prec == GS_MOM_FP8E4M3) return GS_ERR_UNSUPPORTED;
 
     gs_opt *o = new (std::nothrow) gs_opt;
     if (!o) return GS_ERR_OOM;
@@ -353,7 +385,7 @@ gs_status gs_opt_init(gs_opt **out, const gs_opt_config *cfg, int64_t n_rows, vo
         gs_opt_destroy(o);
         return GS_ERR_OOM;
     }
-    const size_t sbytes = state_row_bytes(c.prec) * (size_t)o->capacity;
+    const size_t sbytes = state_bytes(c.prec, o->capacity);
     if ((e = cudaMemsetAsync(o->m, 0, sbytes, s)) != cudaSuccess || (e = cudaMemsetAsync(o->v, 0, sbytes, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(o->err, 0, sizeof(int32_t), s)) != cudaSuccess ||
         (e = gs::launch_bias_table(c.beta1, c.beta2, o->tab_len, o->tab1, o->tab2, o->fac, s)) != cudaSuccess) {
@@ -415,6 +447,7 @@ gs_status gs_step(gs_opt *o, const gs_attrs *attrs, const gs_grads *grads, const
     if (st != GS_OK) return st;
     const int64_t n = o->n_rows;
     if (!attrs || !grads || !params_ok(o, params)) return GS_ERR_INVALID_ARG;
+    if (terms_unsupported(o, params)) return GS_ERR_UNSUPPORTED;
     if (!attrs_ok(o, *attrs, n) || !attrs_ok(o, *grads, n) || !dev_ok(o, mask, mask ? (size_t)n : 0, 1))
         return GS_ERR_INVALID_ARG;
     StepArgs a;
@@ -432,6 +465,7 @@ gs_status gs_step_camera(gs_opt *o, const gs_attrs *attrs, const gs_grads *grads
     if (st != GS_OK) return st;
     const int64_t n = o->n_rows;
     if (!attrs || !grads || !camera_ok(cam) || !params_ok(o, params)) return GS_ERR_INVALID_ARG;
+    if (terms_unsupported(o, params)) return GS_ERR_UNSUPPORTED;
     if (!attrs_ok(o, *attrs, n) || !attrs_ok(o, *grads, n) || !dev_ok(o, mask_out, mask_out ? (size_t)n : 0, 1) ||
         !dev_ok(o, n_visible, n_visible ? 8 : 0, 8))
         return GS_ERR_INVALID_ARG;
@@ -452,6 +486,7 @@ gs_status gs_step_host(gs_opt *o, const gs_attrs *attrs, const gs_grads *gh, con
     if (st != GS_OK) return st;
     const int64_t n = o->n_rows;
     if (!attrs || !gh || !camera_ok(cam) || !params_ok(o, params) || !n_visible_host) return GS_ERR_INVALID_ARG;
+    if (terms_unsupported(o, params)) return GS_ERR_UNSUPPORTED;
     if (n && (!gh->xyz || !gh->scale || !gh->rot || !gh->opacity || !gh->sh)) return GS_ERR_INVALID_ARG;
     if (!attrs_ok(o, *attrs, n)) return GS_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -554,7 +589,7 @@ gs_status gs_reindex_state(gs_opt *o, const int32_t *src_rows, const uint8_t *re
         if (a != GS_OK) return a;
         o->capacity2 = cap;
     }
-    const gs::StateView out{o->cfg.prec, o->m2, o->v2};
+    const gs::StateView out = view_of(o, o->m2, o->v2, o->capacity2);
     cudaError_t e = gs::launch_reindex(view(o), (int32_t)o->n_rows, out, (int32_t)n_new, src_rows, reset, o->err, s);
     if (e != cudaSuccess) return fail_cuda(o, e);
     std::swap(o->m, o->m2);
@@ -850,6 +885,7 @@ extern "C" gs_status gs_batch_create(gs_batch **out, gs_opt *const *scenes, int3
         if (scenes[s]->cfg.prec != scenes[0]->cfg.prec || scenes[s]->device != scenes[0]->device)
             return GS_ERR_INVALID_ARG;
     }
+    if (scenes[0]->cfg.prec == GS_MOM_FP8E4M3) return GS_ERR_UNSUPPORTED;   // no batched FP8 kernel
     gs_batch *b = new (std::nothrow) gs_batch;
     if (!b) return GS_ERR_OOM;
     b->scenes.assign(scenes, scenes + n_scenes);
@@ -970,6 +1006,7 @@ extern "C" gs_status gs_step_host_noalloc(gs_opt *o, const gs_attrs *attrs, cons
     const int64_t n = o->n_rows;
     if (n > (int64_t)kNaRows) return GS_ERR_INVALID_ARG;
     if (!attrs || !gh || !camera_ok(cam) || !params_ok(o, params) || !n_visible_host) return GS_ERR_INVALID_ARG;
+    if (terms_unsupported(o, params)) return GS_ERR_UNSUPPORTED;
     if (n && (!gh->xyz || !gh->scale || !gh->rot || !gh->opacity || !gh->sh)) return GS_ERR_INVALID_ARG;
     if (!attrs_ok(o, *attrs, n)) return GS_ERR_INVALID_ARG;
     float *base = noalloc_scratch(o->device);

@@ -547,6 +547,7 @@ cudaError_t launch_reindex(const StateView &in, int32_t n_in, const StateView &o
 {
     if (n_out <= 0) return cudaSuccess;
     switch (in.prec) {
+    case GS_MOM_FP8E4M3: return launch_reindex_fp8(in, n_in, out, n_out, src, reset, err, s);
     case GS_MOM_FP32:      // whole 256-B rows (the last 16 B are padding): a warp moves two rows
         reindex_kernel<16, kRowBytesF32><<<blocks_for((int64_t)n_out * 16), kThreads, 0, s>>>(in, n_in, out, n_out,
                                                                                              src, reset, err);
@@ -573,6 +574,7 @@ cudaError_t launch_export(const StateView &st, int32_t n, float *m_out, float *v
                           cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
+    if (st.prec == GS_MOM_FP8E4M3) return launch_export_fp8(st, n, m_out, v_out, t_out, s);
     if (st.prec == GS_MOM_FP16_BLOCK)
         export_f16b_kernel<<<blocks_for((int64_t)n * kNumCols), kThreads, 0, s>>>(st, n, m_out, v_out, t_out);
     else
@@ -584,6 +586,7 @@ cudaError_t launch_import(const StateView &st, int32_t n, const float *m_in, con
                           const uint32_t *t_in, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
+    if (st.prec == GS_MOM_FP8E4M3) return launch_import_fp8(st, n, m_in, v_in, t_in, s);
     if (st.prec == GS_MOM_FP16_BLOCK)
         import_f16b_kernel<<<blocks_for((int64_t)n * 8), kThreads, 0, s>>>(st, n, m_in, v_in, t_in);
     else

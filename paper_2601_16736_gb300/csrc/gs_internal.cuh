@@ -91,6 +91,7 @@ struct StepArgs {
     unsigned long long *n_active;   // optional, accumulated with atomicAdd
     int32_t g_host;              // gradients are pinned host memory read in place
     int32_t tile_ahead;          // CTAs resident at once (0: no look-ahead prefetch)
+    float *msc, *vsc;            // FP8 moments: per-(256-row block, column) scales of m, v
 };
 
 // ------------------------------------------------------- device helpers
@@ -249,7 +250,18 @@ cudaError_t launch_bias_table(double beta1, double beta2, int32_t len, double *t
 struct StateView {
     int prec;
     void *m, *v;
+    float *msc = nullptr, *vsc = nullptr;     // FP8 block scales (64 floats per 256 rows)
 };
+
+// FP8 (e4m3) moments with per-256-row block scales (csrc/step_fp8.cu).
+constexpr int kRowBytesF8 = 64, kF8BlockRows = 256;
+cudaError_t launch_step_fp8(const StepArgs &a, int vis_src, cudaStream_t s);
+cudaError_t launch_export_fp8(const StateView &st, int32_t n, float *m_out, float *v_out, uint32_t *t_out,
+                              cudaStream_t s);
+cudaError_t launch_import_fp8(const StateView &st, int32_t n, const float *m_in, const float *v_in,
+                              const uint32_t *t_in, cudaStream_t s);
+cudaError_t launch_reindex_fp8(const StateView &in, int32_t n_in, const StateView &out, int32_t n_out,
+                               const int32_t *src, const uint8_t *reset, int32_t *err, cudaStream_t s);
 
 cudaError_t launch_reindex(const StateView &in, int32_t n_in, const StateView &out, int32_t n_out,
                            const int32_t *src, const uint8_t *reset, int32_t *err, cudaStream_t s);

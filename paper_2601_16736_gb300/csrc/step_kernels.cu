@@ -238,6 +238,8 @@ cudaError_t launch_tiles(const StepArgs &a, int vis_src, cudaStream_t s)
 cudaError_t launch_step(const StepArgs &a, int prec, int vis_src, cudaStream_t s)
 {
     if (a.n_rows <= 0) return cudaSuccess;
+    if (prec == GS_MOM_FP8E4M3)
+        return (a.noise || a.aiu || a.n_active) ? cudaErrorNotSupported : launch_step_fp8(a, vis_src, s);
     if (a.noise || a.aiu || a.n_active) return launch_step_ext(a, prec, vis_src, s);
     switch (prec) {
     case GS_MOM_FP32: return launch_tiles<GS_MOM_FP32, kShWF32>(a, vis_src, s);

@@ -1,5 +1,6 @@
 """Low-precision moment storage (GS_MOM_BF16, GS_MOM_BF16_HYBRID,
-GS_MOM_FP16_BLOCK) against the FP64 oracle.
+GS_MOM_FP16_BLOCK; GS_MOM_FP8E4M3 in the 1000-step run, the rest of its
+tests in test_gpu_fp8.py) against the FP64 oracle.
 
 Bounds, from the arithmetic: the step computes every moment in FP32 and only
 rounds the stored copy, so after one step from zero state the attributes are
@@ -196,18 +197,24 @@ def _run_sampled(G, orc, wl, prec, sample):
     return got, ref.st.theta, ~diverged
 
 
-@pytest.mark.parametrize("prec,gate", [("FP16_BLOCK", 1e-3), ("BF16_HYBRID", 1e-3), ("BF16", 3e-2)])
+@pytest.mark.parametrize("prec,gate", [("FP16_BLOCK", 1e-3), ("BF16_HYBRID", 1e-3), ("BF16", 3e-2),
+                                       ("FP8E4M3", None)])
 def test_3m_1000_steps_sampled(G, orc, prec, gate):
     """The 3 M-primitive, 1000-step workload (about 20 % visible per view),
-    followed by the oracle on 2000 sampled primitives."""
+    followed by the oracle on 2000 sampled primitives.  FP8 (e4m3, 3 mantissa
+    bits) has no gate: its errors are recorded and pinned only to stay
+    finite and below 1 (no blow-up from a second moment stored as zero)."""
     wl = synth.WORKLOADS["c3_3m"]
     sample = np.sort(np.random.default_rng(17).choice(wl.n, 2000, replace=False))
     got, ref, keep = _run_sampled(G, orc, wl, prec, sample)
-    assert keep.mean() > 0.998
+    assert keep.mean() > (0.9 if gate is None else 0.998)
     errs = group_rel_l2(got, ref, rows=keep)
     print(prec, "group relative L2 after 1000 steps:", errs)
     for g, e in errs.items():
-        assert e <= gate, f"{prec} group {g}: {e:.2e} > {gate:.0e}"
+        if gate is None:
+            assert np.isfinite(e) and e < 1.0, f"{prec} group {g}: {e:.2e}"
+        else:
+            assert e <= gate, f"{prec} group {g}: {e:.2e} > {gate:.0e}"
 
 
 def test_fp16_block_with_optional_terms(G, orc):
