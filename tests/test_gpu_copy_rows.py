@@ -40,7 +40,7 @@ def _same(run, snap):
     assert np.array_equal(t2, t)
 
 
-@pytest.mark.parametrize("prec", ["FP32", "BF16", "BF16_HYBRID", "FP16_BLOCK"])
+@pytest.mark.parametrize("prec", ["FP32", "BF16", "BF16_HYBRID", "FP16_BLOCK", "FP8E4M3"])
 def test_copy_rows_changes_nothing(G, prec):
     n = 60_007
     groups = synth.scene_blobs(n, 131, 12.5)

@@ -381,24 +381,30 @@ def test_bias_table_matches_oracle(G, orc):
     run.close()
 
 
+@pytest.mark.parametrize("prec", ["FP32", "FP16_BLOCK", "FP8E4M3"])
 @pytest.mark.parametrize("pinned", [True, False])
-def test_step_host_equals_device_path(G, pinned):
+def test_step_host_equals_device_path(G, pinned, prec):
     """Pinned host gradients are read in place by the kernel, pageable ones
-    are staged on the device first: both give the device path's result."""
+    are staged on the device first: both give the device path's result,
+    attributes and moments, over two steps."""
     n = 20_000
     groups = synth.scene_blobs(n, 750, 12.5)
-    grads = synth.grads_rows(n, 751)
-    cam = synth.ring_cameras(5)[2]
-    a, b = GpuScene(groups), GpuScene(groups)
-    a.set_grads(grads)
-    p = G.make_params(LR, 1)
-    a.step_camera(cam, p)
-    gh = {k: torch.from_numpy(np.ascontiguousarray(v)) for k, v in synth.from_rows(grads).items()}
-    if pinned:
-        gh = {k: v.pin_memory() for k, v in gh.items()}
-    nv = G.gs_step_host(b.h, G.make_attrs(b.attrs), G.make_attrs(gh), G.make_camera(cam), p)
-    assert nv == int(a.nvis.item())
+    cams = synth.ring_cameras(5)
+    kw = dict(prec=getattr(G, "GS_MOM_" + prec))
+    a, b = GpuScene(groups, **kw), GpuScene(groups, **kw)
+    for k in (1, 2):
+        grads = synth.grads_rows(n, 751, k)
+        a.set_grads(grads)
+        p = G.make_params(LR, k)
+        a.step_camera(cams[k], p)
+        gh = {g: torch.from_numpy(np.ascontiguousarray(v)) for g, v in synth.from_rows(grads).items()}
+        if pinned:
+            gh = {g: v.pin_memory() for g, v in gh.items()}
+        nv = G.gs_step_host(b.h, G.make_attrs(b.attrs), G.make_attrs(gh), G.make_camera(cams[k]), p)
+        assert nv == int(a.nvis.item())
     assert a.rows().tobytes() == b.rows().tobytes()
+    for x, y in zip(a.state(), b.state()):
+        assert x.tobytes() == y.tobytes()
     a.close()
     b.close()
 
