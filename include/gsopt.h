@@ -95,9 +95,9 @@ typedef enum gs_moment_prec {
                                magnitude is scaled into FP16's top binade, so every
                                value within 2^29 of it keeps FP16's 10-bit mantissa.
                                m rounded to nearest, v stochastically (dithered by
-                               +-1/2 FP16 ulp from the same hash, then rounded to
-                               nearest; values further than 2^29 below their
-                               group's largest round to nearest).  128 B per
+                               +-1/2 FP16 ulp from a counter hash per group, then
+                               rounded to nearest; values further than 2^29 below
+                               their group's largest round to nearest).  128 B per
                                moment and row, as BF16.
                                The step count t saturates at 65535 (the
                                bias-correction factors are exactly 1 from step
