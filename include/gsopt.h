@@ -76,11 +76,12 @@ typedef enum gs_moment_prec {
     GS_MOM_BF16 = 1,        /* all 59 columns BF16, round-to-nearest-even             */
     GS_MOM_FP8E4M3 = 2,     /* all 59 columns e4m3 (64 B per moment and row, t in
                                the m row) with one FP32 scale per column and block
-                               of 256 rows: the smallest power of two that puts the
-                               block's largest magnitude within e4m3's 448.  Each
-                               step re-derives the scales of every block from all
-                               256 rows and re-encodes the rows whose column scale
-                               moved.  m rounded to nearest, v stochastically (+-1/2
+                               of 256 rows, a power of two: each step it grows at
+                               once to keep the block's largest magnitude within
+                               e4m3's 448, and shrinks only when it can drop by two
+                               binades or more (import sets the smallest that
+                               fits).  A scale change re-encodes that column in all
+                               256 rows.  m rounded to nearest, v stochastically (+-1/2
                                e4m3 ulp dither, then nearest); a positive v is never
                                stored as zero.  3 mantissa bits: far outside a 1e-3
                                error budget (measured by the tests and the bench).

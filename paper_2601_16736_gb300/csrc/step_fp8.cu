@@ -1,13 +1,16 @@
 // FP8 (e4m3) moments with per-256-row block scales.
 //
-// Storage: m and v rows of 64 bytes (the 59 e4m3 codes in canonical column
-// order, xyz 0-2, scale 3-5, rot 6-9, opacity 10, SH 11-58; bytes 60-63 of
-// the m row hold the step counter t), and for every block of 256 rows one
-// FP32 scale per column for m and one for v (a power of two, 0 for a column
-// that is zero throughout the block).  A value is code x scale.
+// Storage: m and v rows of 64 bytes, the 59 e4m3 codes in work-chunk order
+// (SH 0-47, rotation 48-51, xyz 52-54, opacity 55, scale 56-58; byte 59 is
+// padding and bytes 60-63 of the m row hold the step counter t), so that
+// each 4-value work chunk is one 32-bit word; and for every block of 256
+// rows one FP32 scale per slot for m and one for v (a power of two, 0 for a
+// slot that is zero throughout the block).  A value is code x scale.
 //
-// A block's scale is the smallest power of two that puts the largest
-// magnitude of its column within e4m3's finite range (448).  Sparse Adam
+// A block's scale is a power of two that keeps the largest magnitude of its
+// slot within e4m3's finite range (448): it grows at once when the values
+// need it, and shrinks only when the smallest fitting power of two is two
+// binades or more below it (import sets that smallest one).  Sparse Adam
 // updates only the visible rows of a block, but the scale belongs to all
 // 256, so one CTA takes one block, with its codes staged in shared memory:
 //   0. the largest code magnitude per column over the rows that stay as they
@@ -42,22 +45,6 @@ __device__ __forceinline__ float f8_dec(uint32_t code)
 
 __device__ __forceinline__ uint32_t f8_rn(float x) { return __nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3); }
 
-// Second moment, rounded stochastically: a dither of +-1/2 e4m3 ulp (20
-// random bits, centred, below the 3 mantissa bits e4m3 keeps) then nearest.
-// In e4m3's subnormal range the dither is below the quantum and the value
-// rounds to nearest.  A positive value never becomes zero (the smallest
-// subnormal, 2^-9 of the scale, is kept instead), so m != 0 never meets
-// v = 0 in the direction m^ / (sqrt(v^) + eps).
-__device__ __forceinline__ uint32_t f8_sr(float x, uint32_t rnd)
-{
-    uint32_t u = __float_as_uint(x);
-    const uint32_t e = u & 0x7f800000u;
-    u += (e != 0u && e != 0x7f800000u) ? (rnd & 0xfffffu) - 0x80000u : 0u;
-    uint32_t c = f8_rn(__uint_as_float(u));
-    if ((c & 0x7fu) == 0u && x > 0.f) c = 1u;
-    return c;
-}
-
 __device__ __forceinline__ uint32_t f8_rn_floor(float x)
 {
     uint32_t c = f8_rn(x);
@@ -77,70 +64,159 @@ __device__ __forceinline__ int f8_scale_exp(uint32_t b)
 }
 __device__ __forceinline__ float pow2f(int e) { return __uint_as_float((uint32_t)(e + 127) << 23); }
 
-// Random bits of the stochastic rounding of element (row, column).
-__device__ __forceinline__ uint32_t f8_rnd(const StepArgs &a, int64_t row, int c)
+// Slot of canonical column c (xyz 0-2, scale 3-5, rot 6-9, opacity 10,
+// SH 11-58) in a code row.
+__device__ __forceinline__ int f8_slot(int c)
 {
-    return fmix32((uint32_t)row * 0x9e3779b1u ^ (uint32_t)c * 0x85ebca77u ^ (uint32_t)a.k_ctr * 0xc2b2ae3du ^
+    return c < 3 ? 52 + c : c < 6 ? 56 + (c - 3) : c < 10 ? 48 + (c - 6) : c == 10 ? 55 : c - 11;
+}
+
+constexpr int kF8Chunks = 15;                // 12 SH, rotation, xyz + opacity, scale
+
+// The 4 values of a code word, times their slots' scales.
+__device__ __forceinline__ void f8_dec4(uint32_t w, const float *s, float *x)
+{
+    const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w & 0xffffu), __NV_E4M3);
+    const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w >> 16), __NV_E4M3);
+    const float2 a = __half22float2(__half2(lo)), b = __half22float2(__half2(hi));
+    x[0] = a.x * s[0];
+    x[1] = a.y * s[1];
+    x[2] = b.x * s[2];
+    x[3] = b.y * s[3];
+}
+
+__device__ __forceinline__ uint32_t f8_pack4(float y0, float y1, float y2, float y3)
+{
+    const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(y0, y1), __NV_SATFINITE, __NV_E4M3);
+    const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(y2, y3), __NV_SATFINITE, __NV_E4M3);
+    return (lo & 0xffffu) | (hi << 16);
+}
+
+// First moments of a chunk, to nearest under the inverse scales inv.
+__device__ __forceinline__ uint32_t f8_enc4_rn(const float *x, const float *inv)
+{
+    return f8_pack4(x[0] * inv[0], x[1] * inv[1], x[2] * inv[2], x[3] * inv[3]);
+}
+
+// Second moments of a chunk: each value dithered by +-1/2 e4m3 ulp (20
+// random bits from the chunk's hash times a distinct odd constant, centred,
+// below the 3 mantissa bits kept), then to nearest; a positive value keeps
+// at least the smallest subnormal code.
+__device__ __forceinline__ uint32_t f8_enc4_sr(const float *x, const float *inv, uint32_t h)
+{
+    constexpr uint32_t kOdd[4] = {1u, 0x9e3779b1u, 0x85ebca77u, 0xc2b2ae3du};
+    float y[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        uint32_t u = __float_as_uint(x[e] * inv[e]);
+        const uint32_t ex = u & 0x7f800000u;
+        u += (ex != 0u && ex != 0x7f800000u) ? ((h * kOdd[e]) & 0xfffffu) - 0x80000u : 0u;
+        y[e] = __uint_as_float(u);
+    }
+    uint32_t w = f8_pack4(y[0], y[1], y[2], y[3]);
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+        if (((w >> (8 * e)) & 0x7fu) == 0u && x[e] > 0.f) w |= 1u << (8 * e);
+    return w;
+}
+
+// Random bits of a chunk's stochastic rounding.
+__device__ __forceinline__ uint32_t f8_rnd(const StepArgs &a, int64_t row, int k)
+{
+    return fmix32((uint32_t)row * 0x9e3779b1u ^ (uint32_t)k * 0x85ebca77u ^ (uint32_t)a.k_ctr * 0xc2b2ae3du ^
                   (uint32_t)a.seed ^ 0x165667b1u);
 }
 
-// Attribute and gradient of element (row r, canonical column c), with the
-// column's learning rate and regulariser kind (1: scale, 2: opacity).
-struct F8Elem {
-    float *th;
-    const float *g;
-    float lr;
-    int reg;
-};
-__device__ __forceinline__ F8Elem f8_elem(const StepArgs &a, const int64_t r, const int c)
+// Attributes and gradients of chunk k of row r (n = 3 for the scale chunk;
+// th[3] = g[3] = 0 there).
+__device__ __forceinline__ void f8_load_chunk(const StepArgs &a, const int64_t r, const int k, float *th, float *g)
 {
-    if (c < 3) return {a.a_xyz + r * 3 + c, a.g_xyz + r * 3 + c, a.lr[0], 0};
-    if (c < 6) return {a.a_scale + r * 3 + (c - 3), a.g_scale + r * 3 + (c - 3), a.lr[1], 1};
-    if (c < 10) return {a.a_rot + r * 4 + (c - 6), a.g_rot + r * 4 + (c - 6), a.lr[2], 0};
-    if (c == 10) return {a.a_op + r, a.g_op + r, a.lr[3], 2};
-    return {a.a_sh + r * 48 + (c - 11), a.g_sh + r * 48 + (c - 11), c < 14 ? a.lr[4] : a.lr[5], 0};
+    if (k < 12 || k == 12) {
+        const float *pt = k < 12 ? a.a_sh + r * 48 + 4 * k : a.a_rot + r * 4;
+        const float *pg = k < 12 ? a.g_sh + r * 48 + 4 * k : a.g_rot + r * 4;
+        const float4 x = ld4(pt), y = ldg4_stream(pg);
+        th[0] = x.x; th[1] = x.y; th[2] = x.z; th[3] = x.w;
+        g[0] = y.x; g[1] = y.y; g[2] = y.z; g[3] = y.w;
+    } else if (k == 13) {
+        const float *pt = a.a_xyz + r * 3, *pg = a.g_xyz + r * 3;
+        th[0] = pt[0]; th[1] = pt[1]; th[2] = pt[2]; th[3] = a.a_op[r];
+        g[0] = __ldcs(pg); g[1] = __ldcs(pg + 1); g[2] = __ldcs(pg + 2); g[3] = __ldcs(a.g_op + r);
+    } else {
+        const float *pt = a.a_scale + r * 3, *pg = a.g_scale + r * 3;
+        th[0] = pt[0]; th[1] = pt[1]; th[2] = pt[2]; th[3] = 0.f;
+        g[0] = __ldcs(pg); g[1] = __ldcs(pg + 1); g[2] = __ldcs(pg + 2); g[3] = 0.f;
+    }
 }
 
-// The update of one element in place on its FP32 moments, from its loaded
-// attribute t0 and gradient gv; returns the new attribute.  Visible rows take
-// the Sparse Adam step with the column's learning rate and regulariser
-// (opacity: sig'(tau), scale: exp(kappa), as the other formats' items), then
-// the RSR post-scale when sampled; invisible sampled rows take the RSR
-// scaling alone (Eq. meth::restate).
-__device__ __forceinline__ float f8_apply(const StepArgs &a, const F8Elem &e, const bool vis, const bool smp,
-                                          const float2 f, const float t0, const float gv, float &m, float &v)
+__device__ __forceinline__ void f8_store_chunk(const StepArgs &a, const int64_t r, const int k, const float *th)
 {
-    float t1 = t0;
+    if (k < 12 || k == 12) {
+        st4(k < 12 ? a.a_sh + r * 48 + 4 * k : a.a_rot + r * 4, make_float4(th[0], th[1], th[2], th[3]));
+    } else if (k == 13) {
+        float *pt = a.a_xyz + r * 3;
+        __stcs(pt, th[0]); __stcs(pt + 1, th[1]); __stcs(pt + 2, th[2]);
+        __stcs(a.a_op + r, th[3]);
+    } else {
+        float *pt = a.a_scale + r * 3;
+        __stcs(pt, th[0]); __stcs(pt + 1, th[1]); __stcs(pt + 2, th[2]);
+    }
+}
+
+// The update of chunk k's values in place on their FP32 moments (attributes
+// th in place too).  Visible rows take the Sparse Adam step with each
+// column's learning rate and regulariser (opacity: sig'(tau), scale:
+// exp(kappa), as the other formats' items), then the RSR post-scale when
+// sampled; invisible sampled rows take the RSR scaling alone
+// (Eq. meth::restate).
+__device__ __forceinline__ void f8_apply_chunk(const StepArgs &a, const int k, const bool vis, const bool smp,
+                                               const float2 f, float *th, const float *g, float *m, float *v)
+{
+    const int n = k == 14 ? 3 : 4;
     if (vis) {
-        bool has = false;
-        float gr = 0.f, lam = 0.f, clip = 0.f;
-        if (e.reg == 1 && a.dar_s) { has = true; gr = expf(t0); lam = a.lam_s; clip = a.clip_s; }
-        else if (e.reg == 2 && a.dar_o) { has = true; gr = dsigmoid(t0); lam = a.lam_o; clip = a.clip_o; }
-        t1 = step_element(t0, gv, m, v, f.x, f.y, a, e.lr, has, gr, lam, clip);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            if (e >= n) break;
+            float lr;
+            bool has = false;
+            float gr = 0.f, lam = 0.f, clip = 0.f;
+            if (k < 12) {
+                lr = (k == 0 && e < 3) ? a.lr[4] : a.lr[5];
+            } else if (k == 12) {
+                lr = a.lr[2];
+            } else if (k == 13) {
+                lr = e < 3 ? a.lr[0] : a.lr[3];
+                if (e == 3 && a.dar_o) { has = true; gr = dsigmoid(th[e]); lam = a.lam_o; clip = a.clip_o; }
+            } else {
+                lr = a.lr[1];
+                if (a.dar_s) { has = true; gr = expf(th[e]); lam = a.lam_s; clip = a.clip_s; }
+            }
+            th[e] = step_element(th[e], g[e], m[e], v[e], f.x, f.y, a, lr, has, gr, lam, clip);
+        }
     }
     if (smp) {
-        m *= a.alpha1;
-        v *= a.alpha2;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            m[e] *= a.alpha1;
+            v[e] *= a.alpha2;
+        }
     }
-    return t1;
 }
-
-// Elements per thread whose loads are issued together in the two passes.
-constexpr int kF8Unroll = 4;
 
 template <int kMinBlocks>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) step_fp8(const StepArgs a, const int vis_src)
 {
     constexpr int kWords = kF8Row / 4 - 1;    // code words of a row (the last holds t)
     constexpr int kWarps = kThreads / 32;
-    __shared__ uint4 cm[kF8Tile * kF8Row / 16], cv[kF8Tile * kF8Row / 16];
-    __shared__ float s_old[2][64], s_new[2][64], s_inv[2][64];
+    __shared__ uint32_t cm[kF8Tile * kF8Row / 4], cv[kF8Tile * kF8Row / 4];
+    __shared__ __align__(16) float s_old[2][64], s_inv[2][64];
+    __shared__ float s_new[2][64];
     __shared__ uint32_t s_max[2][64];
     __shared__ uint32_t s_wmax[kWarps][2][kWords];
     __shared__ uint8_t flg[kF8Tile];          // bit 0 visible, bit 1 StSS-sampled
     __shared__ int16_t clist[kF8Tile];        // rows that change (visible or sampled)
     __shared__ float2 fac[kF8Tile];
-    __shared__ int s_nv, s_nc, s_moved;
+    __shared__ int s_nv, s_nc, s_moved;       // s_moved: slots whose scale changed, listed in s_mov
+    __shared__ uint8_t s_mov[2 * 64];         // moment << 6 | slot
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t r0 = (int64_t)blockIdx.x * kF8Tile;
     const int nrow = (int)min((int64_t)kF8Tile, (int64_t)a.n_rows - r0);
@@ -149,8 +225,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) step_fp8(const StepArgs 
     const uint4 *gm = reinterpret_cast<const uint4 *>(static_cast<const char *>(a.m) + r0 * kF8Row);
     const uint4 *gv = reinterpret_cast<const uint4 *>(static_cast<const char *>(a.v) + r0 * kF8Row);
     for (int q = tid; q < nrow * (kF8Row / 16); q += kThreads) {
-        cm[q] = __ldcs(gm + q);
-        cv[q] = __ldcs(gv + q);
+        reinterpret_cast<uint4 *>(cm)[q] = __ldcs(gm + q);
+        reinterpret_cast<uint4 *>(cv)[q] = __ldcs(gv + q);
     }
     if (tid < 64) {
         s_old[0][tid] = tid < kF8Cols ? a.msc[blockIdx.x * 64 + tid] : 0.f;
@@ -181,17 +257,16 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) step_fp8(const StepArgs 
     base = __shfl_sync(0xffffffffu, base, 0);
     if (vis || smp) clist[base + __popc(bal_c & ((1u << lane) - 1u))] = (int16_t)tid;
     if (tid < nrow) {
-        const uint32_t t_old = reinterpret_cast<const uint32_t *>(cm)[tid * (kF8Row / 4) + kF8TWord];
+        const uint32_t t_old = cm[tid * (kF8Row / 4) + kF8TWord];
         const uint32_t tb = a.bias_mode ? a.k_bias : t_old + 1u;
         fac[tid] = (vis && tb < (uint32_t)a.fac_len) ? a.fac[tb] : make_float2(1.0f, 1.0f);
         flg[tid] = (vis ? 1 : 0) | (smp ? 2 : 0);
     }
-    // pass 0: largest code magnitude per column over the rows that stay as
+    // pass 0: largest code magnitude per slot over the rows that stay as
     // they are (e4m3 magnitudes order as their 7-bit codes), bytewise
     {
         const bool keep = tid < nrow && !(vis || smp);
-        const uint32_t *rm = reinterpret_cast<const uint32_t *>(cm) + tid * (kF8Row / 4);
-        const uint32_t *rv = reinterpret_cast<const uint32_t *>(cv) + tid * (kF8Row / 4);
+        const uint32_t *rm = cm + tid * (kF8Row / 4), *rv = cv + tid * (kF8Row / 4);
 #pragma unroll
         for (int w = 0; w < kWords; ++w) {
             uint32_t xm = keep ? rm[w] & 0x7f7f7f7fu : 0u, xv = keep ? rv[w] & 0x7f7f7f7fu : 0u;
@@ -221,102 +296,84 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) step_fp8(const StepArgs 
     }
     __syncthreads();
 
-    // pass 1: the changed rows' new values, into the column maxima
-    const uint8_t *bm = reinterpret_cast<const uint8_t *>(cm), *bv = reinterpret_cast<const uint8_t *>(cv);
-    const int nc = s_nc, total = nc * kF8Cols;
-    for (int b0 = tid; b0 < total; b0 += kF8Unroll * kThreads) {
-        float t0[kF8Unroll], gv[kF8Unroll];
+    // work items: the changed rows' chunks, kind-major (all SH chunks, then
+    // rotation, xyz + opacity, scale) so warps stay convergent
+    const int nc = s_nc, e_sh = 12 * nc, total = kF8Chunks * nc;
+    // pass 1: the changed rows' new values, into the slot maxima
+    for (int w = tid; w < total; w += kThreads) {
+        int j, k;
+        if (w < e_sh) { j = w / 12; k = w - 12 * j; }
+        else { const int q = w - e_sh; k = 12 + q / nc; j = q - (k - 12) * nc; }
+        const int lr = clist[j], fl = flg[lr];
+        float th[4], g[4], m[4], v[4];
+        if (fl & 1) f8_load_chunk(a, r0 + lr, k, th, g);
+        f8_dec4(cm[lr * (kF8Row / 4) + k], &s_old[0][4 * k], m);
+        f8_dec4(cv[lr * (kF8Row / 4) + k], &s_old[1][4 * k], v);
+        f8_apply_chunk(a, k, fl & 1, fl & 2, fac[lr], th, g, m, v);
+        const int n = k == 14 ? 3 : 4;
 #pragma unroll
-        for (int u = 0; u < kF8Unroll; ++u) {          // the visible elements' loads, all in flight
-            const int idx = b0 + u * kThreads;
-            t0[u] = gv[u] = 0.f;
-            if (idx < total) {
-                const int j = idx / kF8Cols, lr = clist[j];
-                if (flg[lr] & 1) {
-                    const F8Elem e = f8_elem(a, r0 + lr, idx - j * kF8Cols);
-                    t0[u] = *e.th;
-                    gv[u] = *e.g;
-                }
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < kF8Unroll; ++u) {
-            const int idx = b0 + u * kThreads;
-            if (idx >= total) continue;
-            const int j = idx / kF8Cols, c = idx - j * kF8Cols, lr = clist[j];
-            const int fl = flg[lr];
-            float m = f8_dec(bm[lr * kF8Row + c]) * s_old[0][c], v = f8_dec(bv[lr * kF8Row + c]) * s_old[1][c];
-            f8_apply(a, f8_elem(a, r0 + lr, c), fl & 1, fl & 2, fac[lr], t0[u], gv[u], m, v);
-            atomicMax(&s_max[0][c], __float_as_uint(fabsf(m)));
-            atomicMax(&s_max[1][c], __float_as_uint(fabsf(v)));
+        for (int e = 0; e < 4; ++e) {
+            if (e >= n) break;
+            atomicMax(&s_max[0][4 * k + e], __float_as_uint(fabsf(m[e])));
+            atomicMax(&s_max[1][4 * k + e], __float_as_uint(fabsf(v[e])));
         }
     }
     __syncthreads();
     if (tid < 2 * kF8Cols) {
+        // the new scale: grows at once to fit the slot's largest magnitude;
+        // shrinks only when it could drop by two binades or more (a scale
+        // change re-encodes the slot in all 256 rows; one binade of slack
+        // costs at most one bit at the bottom of e4m3's range)
         const int w = tid / kF8Cols, c = tid - w * kF8Cols;
         const uint32_t b = s_max[w][c];
-        float s = 0.f, inv = 0.f;
+        const float so = s_old[w][c];
+        float s = so;
         if (b) {
             const int e = f8_scale_exp(b);
-            s = pow2f(e);
-            inv = pow2f(-e);
+            const int eo = so > 0.f ? (int)(__float_as_uint(so) >> 23) - 127 : -1000;
+            if (e > eo || e <= eo - 2) s = pow2f(e);
         }
         s_new[w][c] = s;
-        s_inv[w][c] = inv;
-        if (s != s_old[w][c]) {
+        s_inv[w][c] = s > 0.f ? __frcp_rn(s) : 0.f;      // exact: s is a power of two
+        if (s != so) {
             (w ? a.vsc : a.msc)[blockIdx.x * 64 + c] = s;
-            s_moved = 1;
+            s_mov[atomicAdd(&s_moved, 1)] = (uint8_t)(w << 6 | c);
         }
+    } else if (tid < 2 * kF8Cols + 2) {
+        const int w = tid - 2 * kF8Cols;     // the padding slot: encodes 0
+        s_new[w][kF8Cols] = 0.f;
+        s_inv[w][kF8Cols] = 0.f;
     }
     __syncthreads();
 
     // pass 2: attributes of visible rows, the changed rows' codes under the
     // new scales
-    uint8_t *wm = reinterpret_cast<uint8_t *>(cm), *wvb = reinterpret_cast<uint8_t *>(cv);
-    for (int b0 = tid; b0 < total; b0 += kF8Unroll * kThreads) {
-        float t0[kF8Unroll], gv[kF8Unroll];
-#pragma unroll
-        for (int u = 0; u < kF8Unroll; ++u) {
-            const int idx = b0 + u * kThreads;
-            t0[u] = gv[u] = 0.f;
-            if (idx < total) {
-                const int j = idx / kF8Cols, lr = clist[j];
-                if (flg[lr] & 1) {
-                    const F8Elem e = f8_elem(a, r0 + lr, idx - j * kF8Cols);
-                    t0[u] = *e.th;
-                    gv[u] = *e.g;
-                }
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < kF8Unroll; ++u) {
-            const int idx = b0 + u * kThreads;
-            if (idx >= total) continue;
-            const int j = idx / kF8Cols, c = idx - j * kF8Cols, lr = clist[j];
-            const int fl = flg[lr];
-            float m = f8_dec(wm[lr * kF8Row + c]) * s_old[0][c], v = f8_dec(wvb[lr * kF8Row + c]) * s_old[1][c];
-            const F8Elem e = f8_elem(a, r0 + lr, c);
-            const float t1 = f8_apply(a, e, fl & 1, fl & 2, fac[lr], t0[u], gv[u], m, v);
-            if (fl & 1) __stcs(e.th, t1);
-            wm[lr * kF8Row + c] = (uint8_t)f8_rn(m * s_inv[0][c]);
-            wvb[lr * kF8Row + c] = (uint8_t)f8_sr(v * s_inv[1][c], f8_rnd(a, r0 + lr, c));
-        }
+    for (int w = tid; w < total; w += kThreads) {
+        int j, k;
+        if (w < e_sh) { j = w / 12; k = w - 12 * j; }
+        else { const int q = w - e_sh; k = 12 + q / nc; j = q - (k - 12) * nc; }
+        const int lr = clist[j], fl = flg[lr];
+        float th[4], g[4], m[4], v[4];
+        if (fl & 1) f8_load_chunk(a, r0 + lr, k, th, g);
+        uint32_t *pm = cm + lr * (kF8Row / 4) + k, *pv = cv + lr * (kF8Row / 4) + k;
+        f8_dec4(*pm, &s_old[0][4 * k], m);
+        f8_dec4(*pv, &s_old[1][4 * k], v);
+        f8_apply_chunk(a, k, fl & 1, fl & 2, fac[lr], th, g, m, v);
+        if (fl & 1) f8_store_chunk(a, r0 + lr, k, th);
+        if (k == 14) m[3] = v[3] = 0.f;       // the padding slot
+        *pm = f8_enc4_rn(m, &s_inv[0][4 * k]);
+        *pv = f8_enc4_sr(v, &s_inv[1][4 * k], f8_rnd(a, r0 + lr, k));
     }
-    // the kept rows, re-encoded in the columns whose scale moved
-    if (s_moved) {
-        for (int idx = tid; idx < nrow * kF8Cols; idx += kThreads) {
-            const int lr = idx / kF8Cols, c = idx - lr * kF8Cols;
-            if (flg[lr]) continue;
-            if (s_new[0][c] != s_old[0][c])
-                wm[lr * kF8Row + c] = (uint8_t)f8_rn(f8_dec(wm[lr * kF8Row + c]) * s_old[0][c] * s_inv[0][c]);
-            if (s_new[1][c] != s_old[1][c])
-                wvb[lr * kF8Row + c] = (uint8_t)f8_rn_floor(f8_dec(wvb[lr * kF8Row + c]) * s_old[1][c] * s_inv[1][c]);
-        }
+    // the kept rows, re-encoded in the slots whose scale moved
+    const int nmov = s_moved;
+    for (int idx = tid; idx < nrow * nmov; idx += kThreads) {
+        const int lr = idx / nmov, q = s_mov[idx - lr * nmov], w = q >> 6, c = q & 63;
+        if (flg[lr]) continue;
+        uint8_t *pb = reinterpret_cast<uint8_t *>(w ? cv : cm) + lr * kF8Row + c;
+        const float x = f8_dec(*pb) * s_old[w][c] * s_inv[w][c];
+        *pb = (uint8_t)(w ? f8_rn_floor(x) : f8_rn(x));
     }
-    if (tid < nrow && vis) {                  // the row's own step count (Sec. 3.2)
-        uint32_t *tw = reinterpret_cast<uint32_t *>(cm) + tid * (kF8Row / 4) + kF8TWord;
-        *tw = *tw + 1u;
-    }
+    if (tid < nrow && vis) cm[tid * (kF8Row / 4) + kF8TWord] += 1u;   // the row's own step count (Sec. 3.2)
     __syncthreads();
     // write back the rows that changed: all of them when a scale moved
     uint4 *om4 = reinterpret_cast<uint4 *>(static_cast<char *>(a.m) + r0 * kF8Row);
@@ -324,8 +381,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) step_fp8(const StepArgs 
     const bool all = s_moved != 0;
     for (int q = tid; q < nrow * (kF8Row / 16); q += kThreads) {
         if (!all && !flg[q / (kF8Row / 16)]) continue;
-        __stcs(om4 + q, cm[q]);
-        __stcs(ov4 + q, cv[q]);
+        __stcs(om4 + q, reinterpret_cast<const uint4 *>(cm)[q]);
+        __stcs(ov4 + q, reinterpret_cast<const uint4 *>(cv)[q]);
     }
 }
 
@@ -338,14 +395,14 @@ __global__ void export_fp8_kernel(const uint8_t *__restrict__ m, const uint8_t *
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)n * kF8Cols) return;
     const int64_t r = idx / kF8Cols;
-    const int c = (int)(idx - r * kF8Cols);
+    const int c = f8_slot((int)(idx - r * kF8Cols));
     const int64_t sb = (r / kF8Tile) * 64 + c;
     if (m_out) m_out[idx] = f8_dec(m[r * kF8Row + c]) * msc[sb];
     if (v_out) v_out[idx] = f8_dec(v[r * kF8Row + c]) * vsc[sb];
     if (t_out && c == 0) t_out[r] = reinterpret_cast<const uint32_t *>(m + r * kF8Row)[kF8TWord];
 }
 
-// One CTA per block: the column maxima of the imported values, the scales,
+// One CTA per block: the slot maxima of the imported values, the scales,
 // then the codes (both moments to nearest, a positive v never to zero).  A
 // NULL part keeps the stored one.
 __global__ void __launch_bounds__(kThreads) import_fp8_kernel(uint8_t *__restrict__ m, uint8_t *__restrict__ v,
@@ -363,7 +420,7 @@ __global__ void __launch_bounds__(kThreads) import_fp8_kernel(uint8_t *__restric
     __syncthreads();
     const int64_t e0 = r0 * kF8Cols;
     for (int q = tid; q < nrow * kF8Cols; q += kThreads) {
-        const int c = q % kF8Cols;
+        const int c = f8_slot(q % kF8Cols);
         if (m_in) atomicMax(&s_max[0][c], __float_as_uint(fabsf(m_in[e0 + q])));
         if (v_in) atomicMax(&s_max[1][c], __float_as_uint(fabsf(v_in[e0 + q])));
     }
@@ -379,7 +436,7 @@ __global__ void __launch_bounds__(kThreads) import_fp8_kernel(uint8_t *__restric
     }
     __syncthreads();
     for (int q = tid; q < nrow * kF8Cols; q += kThreads) {
-        const int lr = q / kF8Cols, c = q - lr * kF8Cols;
+        const int lr = q / kF8Cols, c = f8_slot(q - lr * kF8Cols);
         if (m_in) m[(r0 + lr) * kF8Row + c] = (uint8_t)f8_rn(m_in[e0 + q] * s_inv[0][c]);
         if (v_in) v[(r0 + lr) * kF8Row + c] = (uint8_t)f8_rn_floor(v_in[e0 + q] * s_inv[1][c]);
     }
@@ -390,8 +447,9 @@ __global__ void __launch_bounds__(kThreads) import_fp8_kernel(uint8_t *__restric
 // One CTA per output block.  Output row j takes the state of old row
 // src[j] (src[j] < 0 or reset[j]: zero moments and t = 0), decoded with the
 // old row's block scales and re-encoded under the output block's new
-// scales (both moments to nearest, a positive v never to zero).  An
-// out-of-range source is not read: the row is zeroed and the error word set.
+// scales (both moments to nearest, a positive v never to zero), slot by
+// slot.  An out-of-range source is not read: the row is zeroed and the
+// error word set.
 __global__ void __launch_bounds__(kThreads) reindex_fp8_kernel(
     const uint8_t *__restrict__ m_in, const uint8_t *__restrict__ v_in, const float *__restrict__ msc_in,
     const float *__restrict__ vsc_in, int32_t n_in, uint8_t *__restrict__ m_out, uint8_t *__restrict__ v_out,
