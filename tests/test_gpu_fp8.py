@@ -2,12 +2,14 @@
 
 Bounds, from the arithmetic.  The step computes every moment in FP32 and
 only the stored copy is rounded, so after one step from zero state the
-attributes equal the FP32 path's bit for bit.  A stored moment x of a block
-whose column scale is s (the smallest power of two with amax / s <= 448) is
-within half an e4m3 ulp, 2^-4 |x|, where x / s is normal (>= 2^-6), and within
-half the subnormal spacing, 2^-10 s, below; the second moment, rounded
-stochastically, within one ulp (2^-3 |x| or 2^-9 s); a positive second moment
-is never stored as zero.  Over many steps the rounded moments feed back: the
+attributes equal the FP32 path's bit for bit, and every block scale s is the
+smallest power of two with amax / s <= 448 (from zero state a scale only
+grows to fit; later steps shrink it only by two binades or more).  A stored
+moment x is then within half an e4m3 ulp, 2^-4 |x|, where x / s is normal
+(>= 2^-6), and within half the subnormal spacing, 2^-10 s, below; the second
+moment, rounded stochastically, within one ulp (2^-3 |x| or 2^-9 s); a
+positive second moment is never stored as zero.  Import sets the smallest
+fitting scales.  Over many steps the rounded moments feed back: the
 3 M, 1000-step workload's group errors are recorded (far outside the 1e-3
 budget of the mixed-precision gate) and pinned only to stay bounded.
 
