@@ -515,10 +515,11 @@ def next_rows_leg(G, synth, steps, warmup=10, aiu_prob=0.1):
     return out
 
 
-def density_sweep(G, synth, densities=(1.0, 0.6, 0.3, 0.1, 0.05), steps=200, warmup=20):
-    """The plain FP32 step on the 1 M scene with caller masks of random rows
-    at each density: how the achieved bandwidth depends on how scattered the
-    visible rows are."""
+def density_sweep(G, synth, densities=(1.0, 0.6, 0.3, 0.1, 0.05), steps=200, warmup=20, prec="fp32"):
+    """The plain step (moments in `prec`) on the 1 M scene with caller masks
+    of random rows at each density: how the achieved bandwidth depends on how
+    scattered the visible rows are.  Each density also reports the time per
+    step, so formats compare directly."""
     import torch
     wl = synth.WORKLOADS[WORKLOAD]
     n = wl.n
@@ -527,10 +528,10 @@ def density_sweep(G, synth, densities=(1.0, 0.6, 0.3, 0.1, 0.05), steps=200, war
     gen = torch.Generator(device="cuda").manual_seed(1)
     gb = [{nm: torch.randn((n, w), generator=gen, device="cuda") * 1e-3 for nm, w in synth.GROUPS} for _ in range(4)]
     A, GB = G.make_attrs(attrs), [G.make_attrs(g) for g in gb]
-    h = G.gs_opt_init(G.make_config(n_pixels=wl.n_pixels), n)
+    h = G.gs_opt_init(G.make_config(n_pixels=wl.n_pixels, prec=PREC_ENUM[prec]), n)
     rng = np.random.default_rng(0)
     peak, _ = _peaks()
-    out = {"workload": f"{wl.name} scene, random-row masks, fp32 moments, {steps} steps per density"}
+    out = {"workload": f"{wl.name} scene, random-row masks, {prec} moments, {steps} steps per density"}
     for dens in densities:
         masks = [torch.from_numpy((rng.random(n) < dens).astype(np.uint8)).cuda() for _ in range(4)]
         nvis = [int(m.sum().item()) for m in masks]
@@ -546,7 +547,7 @@ def density_sweep(G, synth, densities=(1.0, 0.6, 0.3, 0.1, 0.05), steps=200, war
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
         nv = sum(nvis[i % 4] for i in range(warmup, warmup + steps)) / steps
-        gbs = (nv * (3 * 236 + STATE_RW["fp32"] + 8 - 12 + 12) + n) / ms / 1e6    # + xyz of visible rows, mask
+        gbs = (nv * (3 * 236 + STATE_RW[prec] + T_RW[prec]) + n) / ms / 1e6    # visible rows' bytes, mask
         out[str(dens)] = {"ms": ms, "hbm_gbs": gbs, "frac": gbs / peak}
     G.gs_opt_destroy(h)
     return out
@@ -839,7 +840,7 @@ def main():
         B.build()
         from paper_2601_16736_gb300 import gsopt as G
         from paper_2601_16736_gb300 import synth
-        print(json.dumps({"density_sweep": density_sweep(G, synth)}))
+        print(json.dumps({"density_sweep": density_sweep(G, synth, prec=args.prec)}))
     else:
         run_ours(args)
 
