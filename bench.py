@@ -553,22 +553,25 @@ def density_sweep(G, synth, densities=(1.0, 0.6, 0.3, 0.1, 0.05), steps=200, war
     return out
 
 
-HYB_STATE = 2 * (14 * 4 + 45 * 2) + 4     # m, v and t of one row in the hybrid format (B)
+# m, v and t of one row as the re-index moves them (B): hybrid (14 FP32 and 45
+# BF16 columns per moment, t inside), FP16 block (59 FP16 values and 8
+# exponent bytes per moment, uint16 t)
+REINDEX_STATE = {"bf16_hybrid": 2 * (14 * 4 + 45 * 2) + 4, "fp16_block": 2 * (59 * 2 + 8) + 2}
 
 
-def reindex_leg(G, synth, steps, prec="bf16_hybrid", n_events=3):
-    """The 6 M workload (about 10 % visible) with BF16-hybrid moments and a
+def reindex_leg(G, synth, steps, precs=("fp16_block", "bf16_hybrid"), n_events=3):
+    """The 6 M workload (about 10 % visible) with mixed-precision moments and a
     row-set change every 100 steps: prune 5 %, clone 5 % (fresh state),
     relocate 2 % (destination state reset).  Each event re-indexes the
     library's state (gs_reindex_state) and gathers the attributes into the
     second attribute buffer (gs_gather_attrs); both run inside the timed
-    region.  The events' index arrays are resident on the device."""
+    region.  The events' index arrays are resident on the device.  One run per
+    moment format in `precs`, from the same scene."""
     import torch
     wl = synth.WORKLOADS["c5_6m"]
     warm = wl.restate_every                   # the first event (spare state allocation) is a warm-up
     sc = Scene(G, synth, wl, wl.seed, warm + steps)
     other = {k: torch.empty_like(v) for k, v in sc.attrs.items()}
-    bufs = [(sc.attrs, sc.A), (other, G.make_attrs(other))]
     events = []
     for e in range(n_events):
         src, reset, attr_src = synth.reindex_event(wl.n, wl.seed, e)
@@ -576,55 +579,63 @@ def reindex_leg(G, synth, steps, prec="bf16_hybrid", n_events=3):
         events.append(dict(src=torch.from_numpy(src).cuda(), reset=torch.from_numpy(reset).cuda(),
                            attr_src=torch.from_numpy(attr_src).cuda(),
                            n_copy=int(((src >= 0) & (reset == 0)).sum())))
-    h = G.gs_opt_init(G.make_config(n_pixels=wl.n_pixels, prec=PREC_ENUM[prec]), wl.n)
-    counts = torch.zeros(warm + steps, dtype=torch.int64, device="cuda")
-    stream = torch.cuda.current_stream()
-    cur = [0]
-    ev_pairs = []
-    moved = [0.0]
+    out = {}
+    for prec in precs:
+        sc.reset()
+        bufs = [(sc.attrs, sc.A), (other, G.make_attrs(other))]
+        state = REINDEX_STATE[prec]
+        h = G.gs_opt_init(G.make_config(n_pixels=wl.n_pixels, prec=PREC_ENUM[prec]), wl.n)
+        counts = torch.zeros(warm + steps, dtype=torch.int64, device="cuda")
+        stream = torch.cuda.current_stream()
+        cur = [0]
+        ev_pairs = []
+        moved = [0.0]
 
-    def step(i, timed):
-        k = i + 1
-        A = bufs[cur[0]][1]
-        G.gs_step_camera(h, A, sc.GB[i % len(sc.GB)], sc.CAMS[sc.order[i]], sc.P[i], n_visible=counts[i:i + 1],
-                         stream=stream)
-        if k % wl.restate_every == 0:
-            ev = events[(k // wl.restate_every) % n_events]
-            if timed:
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-            G.gs_reindex_state(h, ev["src"], ev["reset"], wl.n, stream=stream)
-            G.gs_gather_attrs(h, A, wl.n, bufs[1 - cur[0]][1], ev["attr_src"], wl.n, stream=stream)
-            cur[0] = 1 - cur[0]
-            if timed:
-                e1.record(stream)
-                ev_pairs.append((e0, e1))
-                moved[0] += ev["n_copy"] * HYB_STATE + wl.n * (HYB_STATE + 5) + wl.n * (2 * 236 + 4)
+        def step(i, timed):
+            k = i + 1
+            A = bufs[cur[0]][1]
+            G.gs_step_camera(h, A, sc.GB[i % len(sc.GB)], sc.CAMS[sc.order[i]], sc.P[i],
+                             n_visible=counts[i:i + 1], stream=stream)
+            if k % wl.restate_every == 0:
+                ev = events[(k // wl.restate_every) % n_events]
+                if timed:
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                G.gs_reindex_state(h, ev["src"], ev["reset"], wl.n, stream=stream)
+                G.gs_gather_attrs(h, A, wl.n, bufs[1 - cur[0]][1], ev["attr_src"], wl.n, stream=stream)
+                cur[0] = 1 - cur[0]
+                if timed:
+                    e1.record(stream)
+                    ev_pairs.append((e0, e1))
+                    moved[0] += ev["n_copy"] * state + wl.n * (state + 5) + wl.n * (2 * 236 + 4)
 
-    for i in range(warm):
-        step(i, False)
-    torch.cuda.synchronize()
-    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    for i in range(warm, warm + steps):
-        step(i, True)
-    t1.record(stream)
-    torch.cuda.synchronize()
-    assert G.gs_opt_sync_errors(h) == 0
-    G.gs_opt_destroy(h)
-    elapsed = t0.elapsed_time(t1) / 1e3
-    nv = int(counts[warm:].sum().item())
-    re_s = sum(a.elapsed_time(b) for a, b in ev_pairs) / 1e3
-    res = {"workload": f"{wl.name}: {wl.n} Gaussians, ~{nv / steps / wl.n:.0%} visible, {prec} moments, "
-                       f"re-index every {wl.restate_every} steps (prune 5 %, clone 5 %, relocate 2 %)",
-           "value": nv / elapsed, "unit": UNIT, "steps": steps, "ms_per_step": elapsed / steps * 1e3,
-           "events": len(ev_pairs), "reindex_ms_per_event": re_s / max(len(ev_pairs), 1) * 1e3,
-           "reindex_share_of_time": re_s / elapsed,
-           "reindex_gbs": moved[0] / re_s / 1e9 if re_s > 0 else None,
-           "reindex_bytes_per_event": moved[0] / max(len(ev_pairs), 1)}
+        for i in range(warm):
+            step(i, False)
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for i in range(warm, warm + steps):
+            step(i, True)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        assert G.gs_opt_sync_errors(h) == 0
+        G.gs_opt_destroy(h)
+        if cur[0]:                            # leave the scene's attributes in their own buffer
+            for k in sc.attrs:
+                sc.attrs[k].copy_(other[k])
+        elapsed = t0.elapsed_time(t1) / 1e3
+        nv = int(counts[warm:].sum().item())
+        re_s = sum(a.elapsed_time(b) for a, b in ev_pairs) / 1e3
+        out[prec] = {"workload": f"{wl.name}: {wl.n} Gaussians, ~{nv / steps / wl.n:.0%} visible, {prec} moments, "
+                                 f"re-index every {wl.restate_every} steps (prune 5 %, clone 5 %, relocate 2 %)",
+                     "value": nv / elapsed, "unit": UNIT, "steps": steps, "ms_per_step": elapsed / steps * 1e3,
+                     "events": len(ev_pairs), "reindex_ms_per_event": re_s / max(len(ev_pairs), 1) * 1e3,
+                     "reindex_share_of_time": re_s / elapsed,
+                     "reindex_gbs": moved[0] / re_s / 1e9 if re_s > 0 else None,
+                     "reindex_bytes_per_event": moved[0] / max(len(ev_pairs), 1)}
     del sc
     torch.cuda.empty_cache()
-    return res
+    return out
 
 
 def batched_leg(G, synth, steps, n_scenes=16, seed=1004, prec="fp32"):
