@@ -52,8 +52,8 @@ BYTES_ROW_VIS = 12          # every row: the mean read by the frustum test
 # DRAM bytes (read + write) of one step_tile launch from an ncu capture of the
 # current kernel, with the algorithmic bytes of that same launch
 # (profiles/step_tile_c2_1m.md).
-NCU_TRAFFIC = {("c2_1m", "fp32"): (545.266944e6, 476.3e6),
-               ("c2_1m", "fp16_block"): (396.978688e6, 351.2e6)}
+NCU_TRAFFIC = {("c2_1m", "fp32"): (544.621568e6, 476.3e6),
+               ("c2_1m", "fp16_block"): (403.216384e6, 351.2e6)}
 
 
 def bytes_visible(prec: str) -> int:

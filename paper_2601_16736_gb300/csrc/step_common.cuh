@@ -580,6 +580,46 @@ __device__ __forceinline__ void sh_item(const StepArgs &a, const int32_t row, co
                                         const float2 f)
 {
     using S = State<kPrec>;
+    if constexpr (kPrec == GS_MOM_FP16_BLOCK) {
+        // Register-lean order, same arithmetic as step_element: the moments
+        // and the directions u first (gradients then dead), m and v encoded
+        // and stored, and only then the attributes loaded and updated.  24
+        // values live at most instead of 32.
+        float m[kW], v[kW], u[kW];
+        uint32_t t = 0;
+        S::template load_sh<kW>(a, row, i, m, v, t);
+        const size_t off = (size_t)row * 48 + kW * i;
+#pragma unroll
+        for (int q = 0; q < kW / 4; ++q) {
+            const float4 y = ldg4_stream(a.g_sh + off + 4 * q);
+            const float gq[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                float &mm = m[4 * q + e], &vv = v[4 * q + e];
+                mm = fmaf(a.c1, gq[e] - mm, mm);
+                vv = fmaf(a.c2, fmaf(gq[e], gq[e], -vv), vv);
+                u[4 * q + e] = __fdividef(mm * f.x, fmaf(sqrt_approx(vv), f.y, a.eps));
+            }
+        }
+        if (sampled) {                     // RSR post-scale (Eq. meth::restate)
+#pragma unroll
+            for (int e = 0; e < kW; ++e) {
+                m[e] *= a.alpha1;
+                v[e] *= a.alpha2;
+            }
+        }
+        S::template store_sh<kW>(a, row, i, m, v, t);
+#pragma unroll
+        for (int q = 0; q < kW / 4; ++q) {
+            const float4 x = ld4(a.a_sh + off + 4 * q);
+            float xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                xs[e] = fmaf(-((i == 0 && 4 * q + e < 3) ? a.lr[4] : a.lr[5]), u[4 * q + e], xs[e]);
+            st4(a.a_sh + off + 4 * q, make_float4(xs[0], xs[1], xs[2], xs[3]));
+        }
+        return;
+    }
     float m[kW], v[kW], th[kW], g[kW];
     uint32_t t = 0;
     S::template load_sh<kW>(a, row, i, m, v, t);

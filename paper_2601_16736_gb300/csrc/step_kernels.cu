@@ -125,21 +125,26 @@ __device__ __forceinline__ void tile_items(const StepArgs &a, const TileLists<kT
 {
     constexpr int kNsh = 48 / kW, kItems = kNsh + kSmallItems<kPrec>;
     const int e_sh = kNsh * nv, e_vis = kItems * nv, e_all = e_vis + kItems * nr;
-    for (int w = threadIdx.x; w < e_all; w += kThreads) {
-        if (w < e_sh) {
-            const int j = w / kNsh, i = w - j * kNsh;
-            const int32_t e = L.list[j];
-            sh_item<kPrec, kW>(a, e & 0x7fffffff, i, e < 0, L.fac[j]);
-        } else if (w < e_vis) {
-            const int q = w - e_sh;
-            const int j = q % nv, c = 12 + q / nv;
-            const int32_t e = L.list[j];
-            small_item<kPrec>(a, e & 0x7fffffff, c, e < 0, L.fac[j]);
-        } else {
-            const int q = w - e_vis;
-            const int j = q / kItems, i = q - j * kItems;
-            rsr_item<kPrec, kW>(a, L.rlist[j], i);
-        }
+    // One flat item space, walked as three loops (SH items, small items, RSR
+    // items) with the same item-to-thread assignment as a single loop: the
+    // kinds no longer share a loop body, so their register demands do not
+    // add up (FP16 block then fits 5 CTAs per SM).
+    int w = threadIdx.x;
+    for (; w < e_sh; w += kThreads) {
+        const int j = w / kNsh, i = w - j * kNsh;
+        const int32_t e = L.list[j];
+        sh_item<kPrec, kW>(a, e & 0x7fffffff, i, e < 0, L.fac[j]);
+    }
+    for (; w < e_vis; w += kThreads) {
+        const int q = w - e_sh;
+        const int j = q % nv, c = 12 + q / nv;
+        const int32_t e = L.list[j];
+        small_item<kPrec>(a, e & 0x7fffffff, c, e < 0, L.fac[j]);
+    }
+    for (; w < e_all; w += kThreads) {
+        const int q = w - e_vis;
+        const int j = q / kItems, i = q - j * kItems;
+        rsr_item<kPrec, kW>(a, L.rlist[j], i);
     }
 }
 
@@ -211,12 +216,12 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) step_batch(const BatchPa
 }  // namespace
 
 constexpr int kStepTile = 256;
-// CTAs of 256 threads resident per SM: 5 (51 registers, no spills) for FP32
-// moments, where the extra warps hide more DRAM latency (1-5 % faster than
-// 4); 4 (64 registers) for the other formats, whose conversions need the
-// registers (5 was slower or equal for them).
+// CTAs of 256 threads resident per SM: 5 (51 registers) for FP32 moments (no
+// spills) and FP16 block (a few spilled words), where the extra warps hide
+// more DRAM latency (FP32 1-5 %, FP16 block up to 7.5 % at 10 % visible
+// faster than 4); 4 (64 registers) for the BF16 formats (5 was slower).
 template <int kPrec>
-constexpr int kStepMinBlocks = kPrec == GS_MOM_FP32 ? 5 : 4;
+constexpr int kStepMinBlocks = (kPrec == GS_MOM_FP32 || kPrec == GS_MOM_FP16_BLOCK) ? 5 : 4;
 constexpr int kShWF32 = 4, kShWBf16 = 8;   // SH columns per item
 
 namespace {
@@ -303,6 +308,7 @@ const BatchCandidate kCandHyb[] = {
 const BatchCandidate kCandF16B[] = {
     {256, 8, 4, launch_batch_t<256, 4, GS_MOM_FP16_BLOCK, 8>},
     {512, 8, 4, launch_batch_t<512, 4, GS_MOM_FP16_BLOCK, 8>},
+    {256, 8, 5, launch_batch_t<256, 5, GS_MOM_FP16_BLOCK, 8>},
 };
 
 const BatchCandidate *candidates(int prec, int *n)
@@ -311,7 +317,7 @@ const BatchCandidate *candidates(int prec, int *n)
     case GS_MOM_FP32: *n = 6; return kCandF32;
     case GS_MOM_BF16: *n = 3; return kCandBf16;
     case GS_MOM_BF16_HYBRID: *n = 3; return kCandHyb;
-    case GS_MOM_FP16_BLOCK: *n = 2; return kCandF16B;
+    case GS_MOM_FP16_BLOCK: *n = 3; return kCandF16B;
     default: *n = 0; return nullptr;
     }
 }

@@ -46,7 +46,7 @@ def test_batch_equals_single_scene_steps(G, prec):
     runs_b, runs_s, cams = _scenes(prec, G)
     b = G.gs_batch_create([r.h for r in runs_b])
     nvis = torch.zeros(len(SIZES), dtype=torch.int64, device="cuda")
-    n_cand = {"FP32": 6, "BF16_HYBRID": 3, "FP16_BLOCK": 2}[prec]
+    n_cand = {"FP32": 6, "BF16_HYBRID": 3, "FP16_BLOCK": 3}[prec]
     steps = 3 * n_cand + 6                  # tuning, then the tuned eager and graph paths
     for k in range(1, steps + 1):
         for s, (rb, rs) in enumerate(zip(runs_b, runs_s)):
