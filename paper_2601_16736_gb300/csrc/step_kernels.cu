@@ -216,12 +216,12 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) step_batch(const BatchPa
 }  // namespace
 
 constexpr int kStepTile = 256;
-// CTAs of 256 threads resident per SM: 5 (51 registers) for FP32 moments (no
-// spills) and FP16 block (a few spilled words), where the extra warps hide
-// more DRAM latency (FP32 1-5 %, FP16 block up to 7.5 % at 10 % visible
-// faster than 4); 4 (64 registers) for the BF16 formats (5 was slower).
+// CTAs of 256 threads resident per SM: 5 (51 registers; no spills except a
+// few words for FP16 block), where the extra warps hide more DRAM latency
+// than 4 CTAs of 64 registers do (measured: FP32 1-5 %, FP16 block up to
+// 7.5 %, BF16 4.6 %, hybrid 2 % faster on the 3 M workload).
 template <int kPrec>
-constexpr int kStepMinBlocks = (kPrec == GS_MOM_FP32 || kPrec == GS_MOM_FP16_BLOCK) ? 5 : 4;
+constexpr int kStepMinBlocks = 5;
 constexpr int kShWF32 = 4, kShWBf16 = 8;   // SH columns per item
 
 namespace {
