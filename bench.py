@@ -49,11 +49,10 @@ STATE_RW = {"fp32": 4 * 236, "bf16_hybrid": 4 * (45 * 2 + 14 * 4), "bf16": 4 * 1
 T_RW = {"fp32": 8, "bf16_hybrid": 8, "bf16": 8, "fp16_block": 4, "fp8_e4m3": 8}
 PREC_ENUM = {"fp32": 0, "bf16": 1, "fp8_e4m3": 2, "bf16_hybrid": 3, "fp16_block": 4}
 BYTES_ROW_VIS = 12          # every row: the mean read by the frustum test
-# DRAM bytes (read + write) of one step_tile launch from an ncu capture of the
-# current kernel, with the algorithmic bytes of that same launch
-# (profiles/step_tile_c2_1m.md).
-NCU_TRAFFIC = {("c2_1m", "fp32"): (544.621568e6, 476.3e6),
-               ("c2_1m", "fp16_block"): (403.216384e6, 351.2e6)}
+# The sources of the step kernel; the DRAM traffic of an ncu capture is
+# reported only while they match the capture's record of them.
+KERNEL_SOURCES = ("paper_2601_16736_gb300/csrc/step_kernels.cu", "paper_2601_16736_gb300/csrc/step_common.cuh",
+                  "paper_2601_16736_gb300/csrc/gs_internal.cuh")
 
 
 def bytes_visible(prec: str) -> int:
@@ -141,14 +140,34 @@ def reduce_over_ranks(dist, elapsed: float, units: int, device: str):
     return float(t[0]), float(u[0])
 
 
+def rsr_offset(warmup: int, steps: int, every: int) -> int:
+    """Iteration offset k0 (step i of a run is iteration k0 + i + 1) that puts
+    an RSR event (k = 0 mod `every`, Eq. meth::restate with the StSS interval
+    of the appendix) inside the timed steps warmup+1 .. warmup+steps, near
+    their middle, whatever `steps` is."""
+    return (-(warmup + (steps + 1) // 2)) % every
+
+
+def headline_plan(warmup: int, steps: int, e2e_steps: int, every: int, e2e_warmup: int = 3):
+    """(k0, n): the iteration offset of the headline run and the number of
+    steps its scene must hold: the device-timed run uses steps 0 .. warmup +
+    steps - 1 and the end-to-end leg steps 0 .. e2e_warmup + e2e_steps - 1."""
+    return rsr_offset(warmup, steps, every), max(warmup + steps, e2e_warmup + e2e_steps)
+
+
 class Scene:
     """One workload resident on the GPU: attributes, a pool of gradient
-    buffers, cameras and the per-step parameters."""
+    buffers, cameras and the per-step parameters of `total_steps` steps.
+    Step i (0-based) of a run is iteration k0 + i + 1; the learning-rate
+    schedule spans the workload's own run length."""
 
-    def __init__(self, G, synth, wl, seed, total_steps):
+    def __init__(self, G, synth, wl, seed, total_steps, k0=0, shuffle=True):
         import torch
-        self.G, self.synth, self.wl, self.seed = G, synth, wl, seed
-        groups = synth.scene_blobs(wl.n, seed, wl.extent) if wl.scene == "blobs" else synth.scene_uniform(wl.n, seed)
+        self.G, self.synth, self.wl, self.seed, self.k0 = G, synth, wl, seed, k0
+        if wl.scene == "blobs":
+            groups = synth.scene_blobs(wl.n, seed, wl.extent, shuffle=shuffle)
+        else:
+            groups = synth.scene_uniform(wl.n, seed)
         self.host_groups = groups
         self.attrs0 = {k: torch.from_numpy(v).cuda() for k, v in groups.items()}
         self.attrs = {k: v.clone() for k, v in self.attrs0.items()}
@@ -158,17 +177,25 @@ class Scene:
             self.gbufs.append({name: torch.randn((wl.n, w), generator=gen, device="cuda", dtype=torch.float32)
                                * (1e-4 if name == "xyz" else 1e-3) for name, w in synth.GROUPS})
         self.cams = wl.cameras()
-        self.order = synth.view_order(len(self.cams), total_steps, seed)
+        self.order = synth.view_order(len(self.cams), max(k0 + total_steps, len(self.cams)), seed)
         self.total = total_steps
         self.A = G.make_attrs(self.attrs)
         self.GB = [G.make_attrs(g) for g in self.gbufs]
         self.CAMS = [G.make_camera(c) for c in self.cams]
-        self.P = [self.params(k) for k in range(1, total_steps + 1)]
+        self.P = [self.params(self.k(i)) for i in range(total_steps)]
+
+    def k(self, i: int) -> int:
+        """Iteration number of step i of a run."""
+        return self.k0 + i + 1
+
+    def cam(self, i: int):
+        """Camera of step i: the random view order, indexed by iteration."""
+        return self.CAMS[self.order[(self.k(i) - 1) % len(self.order)]]
 
     def params(self, k, **extra):
         wl = self.wl
         rs = k % wl.restate_every == 0
-        return self.G.make_params(self.synth.lr_for_step(k, self.total), k, dar_opacity=wl.dar, dar_scale=wl.dar,
+        return self.G.make_params(self.synth.lr_for_step(k, wl.steps), k, dar_opacity=wl.dar, dar_scale=wl.dar,
                                   restate=rs, restate_ratio=wl.restate_ratio, seed=self.seed, **extra)
 
     def reset(self):
@@ -178,23 +205,26 @@ class Scene:
 
 def timed_run(G, sc, prec, steps, warmup, clocks_device=None, dist=None, extra=None):
     """Warm-up then `steps` timed launches of gs_step_camera on a fresh context;
-    CUDA events around the whole region and around every launch.  `extra`:
-    make_params keywords added to every step (the optional terms)."""
+    CUDA events on the launching stream around the whole region and around
+    every launch.  `extra`: make_params keywords added to every step (the
+    optional terms).  Step i of the run is iteration sc.k(i)."""
     import torch
     L = G.lib()
+    if warmup + steps > len(sc.P):
+        raise ValueError(f"scene holds {len(sc.P)} steps, the run needs {warmup + steps}")
     sc.reset()
     h = G.gs_opt_init(G.make_config(n_pixels=sc.wl.n_pixels, prec=PREC_ENUM[prec]), sc.wl.n)
     counts = torch.zeros(warmup + steps, dtype=torch.int64, device="cuda")
     P = sc.P
     if extra:
-        P = [sc.params(k, **extra) for k in range(1, warmup + steps + 1)]
+        P = [sc.params(sc.k(i), **extra) for i in range(warmup + steps)]
     stream = torch.cuda.current_stream()
     sh = ctypes.c_void_p(stream.cuda_stream)
     cnt = counts.data_ptr()
 
     def launch(i):
         s = L.gs_step_camera(h, ctypes.byref(sc.A), ctypes.byref(sc.GB[i % len(sc.GB)]),
-                             ctypes.byref(sc.CAMS[sc.order[i]]), None, ctypes.c_void_p(cnt + 8 * i),
+                             ctypes.byref(sc.cam(i)), None, ctypes.c_void_p(cnt + 8 * i),
                              ctypes.byref(P[i]), sh)
         if s != 0:
             raise G.GsError(s, "gs_step_camera")
@@ -220,19 +250,25 @@ def timed_run(G, sc, prec, steps, warmup, clocks_device=None, dist=None, extra=N
     t1.record(stream)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
+    if dist is not None:
+        dist.barrier()
     clocks = sampler.stop() if sampler else None
     G.gs_opt_destroy(h)
     elapsed = t0.elapsed_time(t1) / 1e3
-    kern = sum(a.elapsed_time(b) for a, b in ev) / 1e3 / steps
+    per = np.array([a.elapsed_time(b) for a, b in ev]) / 1e3
+    kern = float(per.mean())
     nv = counts.cpu().numpy()
     timed_nv = int(nv[warmup:].sum())
-    rsr = 0
+    rsr, rsr_steps = 0, []
     for j in range(steps):
-        k = warmup + 1 + j
+        k = sc.k(warmup + j)
         if k % sc.wl.restate_every == 0:
-            rsr += int(round(sc.wl.restate_ratio * (sc.wl.n - int(nv[k - 1]))))
+            rsr_steps.append(k)
+            rsr += int(round(sc.wl.restate_ratio * (sc.wl.n - int(nv[warmup + j]))))
     byt = (timed_nv * bytes_visible(prec) + steps * sc.wl.n * BYTES_ROW_VIS + rsr * STATE_RW[prec]) / steps
-    return dict(elapsed=elapsed, kern=kern, nv=timed_nv, bytes_per_launch=byt, clocks=clocks, steps=steps)
+    pct = {f"p{q}_ms": float(np.percentile(per, q) * 1e3) for q in (10, 50, 90)}
+    return dict(elapsed=elapsed, kern=kern, nv=timed_nv, bytes_per_launch=byt, clocks=clocks, steps=steps,
+                rsr_steps=rsr_steps, rsr_rows=rsr, **pct)
 
 
 def error_vs_fp32(G, sc, prec, steps=1000):
@@ -253,9 +289,10 @@ def error_vs_fp32(G, sc, prec, steps=1000):
     diverged = torch.zeros(wl.n, dtype=torch.bool, device="cuda")
     for k in range(1, steps + 1):
         i = k - 1
-        p = sc.P[i] if i < len(sc.P) else sc.params(k)
-        G.gs_step_camera(h32, sc.A, sc.GB[i % len(sc.GB)], sc.CAMS[sc.order[i % len(sc.order)]], p, mask_out=m32)
-        G.gs_step_camera(hp, A2, sc.GB[i % len(sc.GB)], sc.CAMS[sc.order[i % len(sc.order)]], p, mask_out=mp)
+        p = sc.params(k)
+        cam = sc.CAMS[sc.order[i % len(sc.order)]]
+        G.gs_step_camera(h32, sc.A, sc.GB[i % len(sc.GB)], cam, p, mask_out=m32)
+        G.gs_step_camera(hp, A2, sc.GB[i % len(sc.GB)], cam, p, mask_out=mp)
         diverged |= m32 != mp
     torch.cuda.synchronize()
     G.gs_opt_destroy(h32)
@@ -268,6 +305,74 @@ def error_vs_fp32(G, sc, prec, steps=1000):
         errs[g] = float((got - ref).norm() / ref.norm().clamp_min(1e-30))
     return {"group_rel_l2_vs_fp32": errs, "max": max(errs.values()), "rows": int(keep.sum().item()),
             "steps": steps}
+
+
+def kernel_source_sha() -> str:
+    """Hash of the sources that define the step kernel: a DRAM traffic figure
+    taken from an ncu capture applies only while these are unchanged."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update((ROOT / f).read_bytes())
+    return h.hexdigest()[:16]
+
+
+def captured_traffic(workload: str, prec: str):
+    """DRAM bytes (read + write) of one step-kernel launch and the algorithmic
+    bytes of that same launch, from the `bench-traffic:` lines of the ncu
+    summaries under profiles/.  Returns (dram, algorithmic, note); dram is
+    None when no capture matches or the kernel sources changed since."""
+    sha = kernel_source_sha()
+    found = None
+    for f in sorted((ROOT / "profiles").glob("*.md")):
+        for line in f.read_text().splitlines():
+            if not line.startswith("bench-traffic:"):
+                continue
+            kv = dict(x.split("=", 1) for x in line.split()[1:] if "=" in x)
+            if kv.get("workload") == workload and kv.get("prec") == prec:
+                found = (kv, f.name)
+    if found is None:
+        return None, None, f"no ncu capture of the {workload} {prec} step kernel"
+    kv, name = found
+    if kv.get("kernel_src_sha") != sha:
+        return None, None, (f"ncu capture in profiles/{name} was taken from kernel sources {kv.get('kernel_src_sha')}, "
+                            f"this build is {sha}: not applicable")
+    return (float(kv["dram_bytes"]), float(kv["algorithmic_bytes"]),
+            f"ncu capture of this kernel build (sources {sha}), profiles/{name}, taken {kv.get('captured')}")
+
+
+def e2e_leg(G, sc, prec, steps, warmup=3):
+    """End to end through the public host-gradient call: every step hands the
+    library FP32 gradients of all rows in pinned host memory (two buffers,
+    alternating) and gets the step's visible count back.  The step kernel
+    reads the visible rows' gradients in place over the CPU-GPU link; the
+    attributes and the optimizer state stay resident on the device.  Timed
+    on the host clock around synchronous calls."""
+    import torch
+    wl = sc.wl
+    gh = [{k: v.cpu().pin_memory() for k, v in g.items()} for g in sc.gbufs[:2]]
+    GH = [G.make_attrs(g) for g in gh]
+    sc.reset()
+    h = G.gs_opt_init(G.make_config(n_pixels=wl.n_pixels, prec=PREC_ENUM[prec]), wl.n)
+    for i in range(warmup):
+        G.gs_step_host(h, sc.A, GH[i % 2], sc.cam(i), sc.P[i])
+    torch.cuda.synchronize()
+    nvs = []
+    tt = time.perf_counter()
+    for j in range(steps):
+        i = warmup + j
+        nvs.append(G.gs_step_host(h, sc.A, GH[i % 2], sc.cam(i), sc.P[i]))
+    dt = time.perf_counter() - tt
+    G.gs_opt_destroy(h)
+    tot = sum(nvs)
+    return {"value": tot / dt, "unit": UNIT, "steps": steps, "ms_per_step": dt / steps * 1e3,
+            "h2d_bytes_per_step": 236 * tot / steps, "d2h_bytes_per_step": 8,
+            "path": ("gs_step_host, one synchronous call per step: all rows' FP32 gradients (236 B per row) sit in "
+                     "pinned host memory, and the step kernel reads the visible rows' gradients in place over the "
+                     "CPU-GPU link (h2d_bytes_per_step = 236 B x the visible rows of each step, counted from the "
+                     "visible counts the calls return); the visible count (8 B) comes back to the host; attributes "
+                     "and optimizer state stay resident on the device"),
+            "host_gradient_bytes_resident": sum(v.numel() * 4 for v in gh[0].values())}
 
 
 def run_ours(args):
@@ -285,32 +390,38 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     wl = synth.WORKLOADS[args.workload]
     seed = replica_seed(wl.seed, rank)
-    sc = Scene(G, synth, wl, seed, args.warmup + args.steps)
+    e2e_steps = args.e2e_steps if args.e2e_steps is not None else args.steps
+    k0, n_scene = headline_plan(args.warmup, args.steps, e2e_steps, wl.restate_every)
+    sc = Scene(G, synth, wl, seed, n_scene, k0=k0)
     r = timed_run(G, sc, args.prec, args.steps, args.warmup, clocks_device=local, dist=dist)
     elapsed, timed_nv = r["elapsed"], r["nv"]
     elapsed_all, nv_all = reduce_over_ranks(dist, elapsed, timed_nv, "cuda")
 
     peak, peak_kind = _peaks()
-    traffic, traffic_ratio = None, None
-    if args.traffic is not None:
-        traffic = args.traffic
-    elif (wl.name, args.prec) in NCU_TRAFFIC:
-        t_bytes, t_alg = NCU_TRAFFIC[(wl.name, args.prec)]
-        traffic, traffic_ratio = t_bytes, t_bytes / t_alg
+    traffic, t_alg, traffic_note = captured_traffic(wl.name, args.prec)
     achieved = r["bytes_per_launch"] / r["kern"] / 1e9
     out = {
         "metric": METRIC, "value": nv_all / elapsed_all, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_all / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{wl.name}: {wl.n} Gaussians, SH3 (59 fp32 attrs), 64 blobs, 200 views, "
-                               f"DAR+RSR(0.1/100), {args.prec} moments, fused visibility+step",
+        "config": {"workload": f"{wl.name}: {wl.n} Gaussians, SH3 (59 fp32 attrs), 64 blobs, 200 views in random "
+                               f"order, DAR+RSR(0.1/100), {args.prec} moments, fused visibility+step",
                    "n_rows": wl.n, "visible_fraction": timed_nv / args.steps / wl.n, "moments": args.prec,
-                   "l2": "inputs larger than L2: 0.94 GB of attributes/grads/state, ~0.5 GB touched per step",
+                   "row_order": "random (shuffled)",
+                   "iterations": f"{sc.k(args.warmup)}-{sc.k(args.warmup + args.steps - 1)} timed "
+                                 f"(warm-up from {sc.k(0)})",
+                   "rsr_steps_timed": r["rsr_steps"],
+                   "l2": "inputs larger than L2: 0.94 GB of attributes/grads/state, ~0.5 GB touched per step; "
+                         "no flush",
                    "parallelism": f"replicas x{ws}"},
+        "p10_ms": r["p10_ms"], "p50_ms": r["p50_ms"], "p90_ms": r["p90_ms"],
         "hbm_gbs": achieved,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "peak_source": peak_kind, "traffic": traffic,
-                     "traffic_over_algorithmic": traffic_ratio,
+                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, copy bandwidth)"
+                                    if peak_kind == "measured" else "fallback 6800 GB/s",
+                     "traffic": traffic,
+                     "traffic_over_algorithmic": traffic / t_alg if traffic else None,
+                     "traffic_source": traffic_note,
                      "bytes_per_launch": r["bytes_per_launch"], "kernel_ms": r["kern"] * 1e3},
         "gpu_launches": args.steps,
         "clocks": r["clocks"],
@@ -322,32 +433,17 @@ def run_ours(args):
         out["mixed_precision_headline"] = {
             "workload": f"{wl.name} (this line's workload), {args.steps} timed steps",
             "fp16_block": {"value": rf["nv"] / rf["elapsed"], "ms_per_step": rf["elapsed"] / args.steps * 1e3,
-                           "hbm_gbs": rf["bytes_per_launch"] / rf["kern"] / 1e9,
+                           "p50_ms": rf["p50_ms"], "hbm_gbs": rf["bytes_per_launch"] / rf["kern"] / 1e9,
                            "speedup_vs_fp32": (rf["nv"] / rf["elapsed"]) / (r["nv"] / r["elapsed"]),
                            "error": error_vs_fp32(G, sc, "fp16_block") if args.mixed_error else None}}
-    if rank == 0 and args.e2e_steps > 0:
-        gh = [{k: v.cpu().pin_memory() for k, v in g.items()} for g in sc.gbufs[:2]]
-        GH = [G.make_attrs(g) for g in gh]
-        h2d = sum(v.numel() * 4 for v in gh[0].values())
-        h = G.gs_opt_init(G.make_config(n_pixels=wl.n_pixels, prec=PREC_ENUM[args.prec]), wl.n)
-        G.gs_step_host(h, sc.A, GH[0], sc.CAMS[0], sc.P[0])
-        torch.cuda.synchronize()
-        tt = time.perf_counter()
-        tot = 0
-        for j in range(args.e2e_steps):
-            tot += G.gs_step_host(h, sc.A, GH[j % 2], sc.CAMS[sc.order[j]], sc.P[j])
-        dt = time.perf_counter() - tt
-        G.gs_opt_destroy(h)
-        out["e2e"] = {"value": tot / dt, "unit": UNIT,
-                      "h2d_bytes_per_step": round(tot / args.e2e_steps * 236) + 64, "d2h_bytes_per_step": 8,
-                      "steps": args.e2e_steps,
-                      "path": "gs_step_host with pinned host gradients (all rows' gradients resident in host "
-                              "memory, 236 MB per step): the step kernel reads the visible rows' gradients in "
-                              "place over the CPU-GPU link; the visible count comes back D2H",
-                      "host_gradient_bytes_per_step": h2d}
+    if rank == 0 and e2e_steps > 0:
+        out["e2e"] = e2e_leg(G, sc, args.prec, e2e_steps)
     del sc
     torch.cuda.empty_cache()
 
+    if rank == 0 and args.secondary:
+        out["row_order_sorted"] = sorted_order_leg(G, synth, wl, args, r)
+        out["c1_100k"] = c1_leg(G, synth, max(args.steps, 200), args.warmup)
     if rank == 0 and args.mixed:
         mwl = synth.WORKLOADS[MIXED_WORKLOAD]
         msc = Scene(G, synth, mwl, mwl.seed, max(1000, args.mixed_steps + 10))
@@ -375,12 +471,55 @@ def run_ours(args):
         out["reindex"] = reindex_leg(G, synth, args.reindex_steps)
     if rank == 0 and args.batched:
         out["batched"] = batched_leg(G, synth, args.batched_steps)
+    if rank == 0 and args.cpu_baseline and args.visibility_band:
+        out["visibility_vs_oracle"] = visibility_leg(G, synth, wl)
     if rank == 0 and args.cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if rank == 0:
         print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def sorted_order_leg(G, synth, wl, args, headline):
+    """The headline workload with its rows grouped by blob instead of shuffled
+    (the same means, attributes and views; rows of one blob are contiguous,
+    so a view's visible rows form long runs): the best case for row locality,
+    beside the random-order headline."""
+    import torch
+    sc = Scene(G, synth, wl, wl.seed, args.warmup + args.steps,
+               k0=rsr_offset(args.warmup, args.steps, wl.restate_every), shuffle=False)
+    r = timed_run(G, sc, args.prec, args.steps, args.warmup)
+    del sc
+    torch.cuda.empty_cache()
+    peak, _ = _peaks()
+    gbs = r["bytes_per_launch"] / r["kern"] / 1e9
+    return {"workload": f"{wl.name} with rows grouped by blob (not shuffled), {args.prec} moments, "
+                        f"{args.steps} timed steps",
+            "value": r["nv"] / r["elapsed"], "ms_per_step": r["elapsed"] / args.steps * 1e3,
+            "p10_ms": r["p10_ms"], "p50_ms": r["p50_ms"], "p90_ms": r["p90_ms"], "hbm_gbs": gbs,
+            "frac": gbs / peak, "visible_fraction": r["nv"] / args.steps / wl.n,
+            "speedup_vs_random_order": (r["nv"] / r["elapsed"]) / (headline["nv"] / headline["elapsed"])}
+
+
+def c1_leg(G, synth, steps, warmup):
+    """The 100 k workload (uniform means, 50 ring views; most rows visible).
+    Its whole working set (about 95 MB of attributes, gradients and FP32
+    state) fits the 129 MB L2, and nothing is flushed between steps, so this
+    is an L2-resident figure, not an HBM one."""
+    import torch
+    wl = synth.WORKLOADS["c1_100k"]
+    sc = Scene(G, synth, wl, wl.seed, warmup + steps, k0=rsr_offset(warmup, steps, wl.restate_every))
+    r = timed_run(G, sc, "fp32", steps, warmup)
+    del sc
+    torch.cuda.empty_cache()
+    return {"workload": f"{wl.name}: {wl.n} Gaussians, uniform means, {wl.n_azimuth} ring views, fp32 moments, "
+                        f"{steps} timed steps",
+            "residency": "L2-resident (working set < 129 MB L2, no flush between steps)",
+            "value": r["nv"] / r["elapsed"], "ms_per_step": r["elapsed"] / steps * 1e3,
+            "p10_ms": r["p10_ms"], "p50_ms": r["p50_ms"], "p90_ms": r["p90_ms"],
+            "gbs_algorithmic": r["bytes_per_launch"] / r["kern"] / 1e9,
+            "visible_fraction": r["nv"] / steps / wl.n}
 
 
 def access_ceiling_leg(G, synth, reps=320, n_views=16):
@@ -720,6 +859,33 @@ def batched_leg(G, synth, steps, n_scenes=16, seed=1004, prec="fp32"):
     return res
 
 
+def visibility_leg(G, synth, wl, n_views=40):
+    """The GPU's frustum decisions on the headline scene against the FP64
+    oracle (part of the oracle leg): for `n_views` of its views, the means
+    within 1e-6 of a frustum plane, the decisions that differ from the
+    oracle's, and those differing farther than 1e-6 from a plane (must be 0)."""
+    import oracle
+    import torch
+    oracle.build()
+    groups = synth.scene_blobs(wl.n, wl.seed, wl.extent)
+    xyz = torch.from_numpy(groups["xyz"]).cuda()
+    h = G.gs_opt_init(G.make_config(n_pixels=wl.n_pixels), wl.n)
+    mask = torch.empty(wl.n, dtype=torch.uint8, device="cuda")
+    cams = wl.cameras()
+    near = differ = far = 0
+    for c in cams[:n_views]:
+        G.gs_visibility(h, xyz, G.make_camera(c), mask)
+        got = mask.cpu().numpy()
+        margin, ref = oracle.frustum_margin_f64(groups["xyz"], c)
+        d = got != ref
+        near += int((np.abs(margin) <= 1e-6).sum())
+        differ += int(d.sum())
+        far += int((d & (np.abs(margin) > 1e-6)).sum())
+    G.gs_opt_destroy(h)
+    return {"workload": f"{wl.name} means, {n_views} views x {wl.n} rows", "means_within_1e-6_of_a_plane": near,
+            "decisions_differing_from_fp64": differ, "differing_beyond_1e-6": far}
+
+
 class OracleSample:
     """The FP64 oracle (single-threaded C) on a bounded sample of the
     workload: the first `rows` primitives of the same scene, stepping through
@@ -747,7 +913,7 @@ class OracleSample:
         self.k += 1
         k = self.k
         cam = self.cams[self.order[k - 1]]
-        mask = o.visibility_f32(self.st.theta[:, 0:3].astype(np.float32), cam)
+        mask = o.visibility(self.st.theta[:, 0:3].astype(np.float32), cam)
         o.step(self.cfg, self.st, self.grads[k % 2], mask, self.synth.lr_for_step(k, wl.steps), wl.dar, wl.dar, k)
         if k % wl.restate_every == 0:
             o.restate(self.cfg, self.st, wl.seed, k, wl.restate_ratio, row_ids=self.ids)
@@ -824,7 +990,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--prec", choices=list(PREC_ENUM), default="fp32")
-    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--e2e-steps", type=int, default=None, help="default: --steps")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-mixed", dest="mixed", action="store_false")
@@ -839,8 +1005,9 @@ def main():
     ap.add_argument("--next-steps", type=int, default=300)
     ap.add_argument("--reindex-steps", type=int, default=1000)
     ap.add_argument("--batched-steps", type=int, default=100)
-    ap.add_argument("--traffic", type=float, default=None,
-                    help="ncu dram bytes per launch of the step kernel for this workload (from profiles/)")
+    ap.add_argument("--no-secondary", dest="secondary", action="store_false",
+                    help="skip the blob-sorted row order and the 100 k (L2-resident) legs")
+    ap.add_argument("--no-visibility-band", dest="visibility_band", action="store_false")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -73,7 +73,9 @@ typedef enum gs_status {
  * GS_MOM_BF16_HYBRID: 3e-4; GS_MOM_FP16_BLOCK: 6e-4). */
 typedef enum gs_moment_prec {
     GS_MOM_FP32 = 0,
-    GS_MOM_BF16 = 1,        /* all 59 columns BF16, round-to-nearest-even             */
+    GS_MOM_BF16 = 1,        /* all 59 columns BF16: m round-to-nearest-even, v
+                               stochastically rounded from a counter hash of (seed,
+                               iteration, row, slot)                              */
     GS_MOM_FP8E4M3 = 2,     /* all 59 columns e4m3 (64 B per moment and row, t in
                                the m row) with one FP32 scale per column and block
                                of 256 rows, a power of two: each step it grows at
@@ -374,15 +376,21 @@ gs_status gs_batch_config(const gs_batch *b, int32_t *tile_rows, int32_t *sh_wid
  * not allowed, or a host runtime that owns the CUDA allocator and forbids
  * allocations behind its back.  This variant stages the gradients in a fixed
  * array that the library keeps in device global memory: a file-scope array
- * sized for GS_NOALLOC_MAX_ROWS rows (about 15.5 MB), reserved on each GPU
- * where the library is used until the process exits.  It calls no cudaMalloc,
- * cudaFree or other allocating routine.
+ * sized for GS_NOALLOC_MAX_ROWS rows (about 15.5 MB).  The array is reserved
+ * on a GPU when the library's code is loaded there: gs_opt_init looks up its
+ * device address (cudaGetSymbolAddress) on the context's device, which also
+ * loads that code under CUDA's lazy module loading, so the reservation happens
+ * at set-up and lasts until the process exits.  gs_step_host_noalloc itself
+ * calls no cudaMalloc, cudaFree or other allocating routine.
  *
  * Arguments, semantics, blocking behaviour and errors are those of
  * gs_step_host, plus: a context with more than GS_NOALLOC_MAX_ROWS rows gives
- * GS_ERR_INVALID_ARG and nothing is launched.  The first call on a device looks
- * up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  Every call in the
+ * GS_ERR_INVALID_ARG and nothing is launched.  If gs_opt_init could not look
+ * the address up, the first call on that device tries again (with the device
+ * current, so make that call before any stream capture) and returns
+ * GS_ERR_CUDA if it fails.  The address is cached per device: after a
+ * cudaDeviceReset the cache is stale, and contexts from before the reset must
+ * not be used anyway.  Every call in the
  * process shares the one array, which keeps the previous call's contents: the
  * visible counter is cleared on each call and the gradient staging is
  * overwritten for all rows.  Calls that overlap on the GPU (other streams,

@@ -181,6 +181,13 @@ def visibility_f32(xyz, cam) -> np.ndarray:
     return mask
 
 
+def visibility(xyz, cam) -> np.ndarray:
+    """The visibility filter V of Eq. meth::sparse_beta, read as the frustum
+    test of the mean, decided in FP64: 1 where the signed distance to every
+    frustum plane (``frustum_margin_f64``) is >= 0."""
+    return frustum_margin_f64(xyz, cam)[1]
+
+
 def frustum_margin_f64(xyz, cam):
     xyz = _req(xyz, np.float32)
     n = xyz.size // 3
@@ -189,6 +196,39 @@ def frustum_margin_f64(xyz, cam):
     mask64 = np.zeros(n, np.uint8)
     lib().orc_frustum_margin_f64(_ptr(xyz), n, _ptr(cam), _ptr(margin), _ptr(mask64))
     return margin, mask64
+
+
+def frustum_fp32_band(xyz, cam) -> np.ndarray:
+    """Per-row bound on |FP64 frustum margin| wherever the FP32 decision of
+    ``visibility_f32`` can differ from the exact (FP64) one.
+
+    The FP32 test evaluates each camera coordinate p_r = sum_j R_rj mu_j + t_r
+    with rounded products summed left to right.  By the inner-product bound
+    (Higham, Accuracy and Stability of Numerical Algorithms, Sec. 3.1) the
+    computed value is within gamma_4 * S_r of the exact one, S_r =
+    sum_j |R_rj mu_j| + |t_r|, gamma_4 = 4u / (1 - 4u), u = 2^-24.  The side
+    test |p_x| <= fl(p_z tan_x) also rounds the product once (u |p_z tan_x|).
+    A decision can flip only where the exact quantity lies within the sum of
+    these errors of zero; divided by the plane normal's length (the margin is
+    a Euclidean distance) that gives, per plane,
+        side x:  (e_x + tan_x e_z + u tan_x (|p_z| + e_z)) / sqrt(1 + tan_x^2)
+        side y:  the same with y
+        near, far:  e_z
+    and the band is the largest of them (plus 1e-12 (1 + S) for the FP64
+    margin's own rounding)."""
+    x = np.asarray(xyz, np.float32).reshape(-1, 3).astype(np.float64)
+    c = np.asarray(cam, np.float32).reshape(16).astype(np.float64)
+    u = 2.0 ** -24
+    g4 = 4 * u / (1 - 4 * u)
+    R = c[:9].reshape(3, 3)
+    t = c[9:12]
+    S = np.abs(x[:, None, :] * R[None, :, :]).sum(axis=2) + np.abs(t)[None, :]
+    e = g4 * S
+    pz = x @ R[2] + t[2]
+    tx, ty = c[12], c[13]
+    bx = (e[:, 0] + tx * e[:, 2] + u * tx * (np.abs(pz) + e[:, 2])) / np.sqrt(1 + tx * tx)
+    by = (e[:, 1] + ty * e[:, 2] + u * ty * (np.abs(pz) + e[:, 2])) / np.sqrt(1 + ty * ty)
+    return np.maximum(np.maximum(bx, by), e[:, 2]) + 1e-12 * (1 + S.max(axis=1))
 
 
 class State:

@@ -9,12 +9,12 @@
  * neither side includes or links the other.
  *
  * Every floating-point quantity of the method is carried in FP64, widened from
- * the FP32 inputs (attributes, gradients).  The one exception is the frustum
- * decision (orc_visibility_f32): the visibility filter is an integer outcome
- * decided by floating point, so the oracle takes that decision in the kernel's
- * precision (FP32, round-to-nearest, no fused multiply-add, fixed evaluation
- * order) and reports the FP64 margin to the nearest frustum plane beside it
- * (orc_frustum_margin_f64).  Compile with -ffp-contract=off.
+ * the FP32 inputs (attributes, gradients).  The visibility filter is decided
+ * in FP64 too, as the sign of the distance to the nearest frustum plane
+ * (orc_frustum_margin_f64).  orc_visibility_f32 is the same test evaluated in
+ * plain FP32 (round-to-nearest, no fused multiply-add, fixed order); the tests
+ * use it to pin how far an FP32 evaluation can stray from the FP64 decision.
+ * Compile with -ffp-contract=off.
  *
  * Row layout (canonical column order of one primitive, 59 values):
  *   0-2   position mu (xyz)
@@ -112,8 +112,9 @@ int32_t orc_stss_sampled(uint64_t seed, int64_t k, int64_t row, double ratio)
  * cam[16] = { R (3x3 row-major world->camera), t (3), tan(fov_x/2),
  *             tan(fov_y/2), z_near, z_far }, camera looks down +z.
  * p = R mu + t;  visible iff z_near <= p.z <= z_far, |p.x| <= p.z tan_x,
- * |p.y| <= p.z tan_y.  Decided in FP32, products rounded before each sum,
- * sums taken left to right.
+ * |p.y| <= p.z tan_y.  Evaluated in FP32, products rounded before each sum,
+ * sums taken left to right: near a plane this can differ from the FP64
+ * decision of orc_frustum_margin_f64, which is the oracle's visibility.
  */
 void orc_visibility_f32(const float *xyz, int64_t n, const float *cam, uint8_t *mask)
 {
@@ -141,8 +142,8 @@ void orc_visibility_f32(const float *xyz, int64_t n, const float *cam, uint8_t *
 /*
  * The same frustum in FP64 as a signed margin: the minimum over the six
  * bounding planes of the Euclidean distance of the mean to the plane, positive
- * inside.  margin >= 0 is the FP64 visibility decision; |margin| is how far the
- * mean is from flipping it (in world units, R being a rotation).
+ * inside.  margin >= 0 is the oracle's visibility decision V; |margin| is how
+ * far the mean is from flipping it (in world units, R being a rotation).
  */
 void orc_frustum_margin_f64(const float *xyz, int64_t n, const float *cam,
                             double *margin, uint8_t *mask64)

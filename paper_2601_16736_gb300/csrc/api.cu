@@ -46,6 +46,10 @@ struct gs_opt {
 
 namespace {
 
+// Device address of gs_step_host_noalloc's fixed staging array on the
+// current device (defined at the end of this file).
+float *noalloc_scratch(int device);
+
 constexpr int64_t kMaxRows = (int64_t)0x7fffffff - 4096;
 constexpr int32_t kMaxTable = 1 << 22;
 
@@ -392,6 +396,10 @@ gs_status gs_opt_init(gs_opt **out, const gs_opt_config *cfg, int64_t n_rows, vo
         gs_opt_destroy(o);
         return GS_ERR_CUDA;
     }
+    // Resolve the allocation-free step's staging array now, so that its
+    // reservation and the symbol lookup happen at set-up rather than in the
+    // first gs_step_host_noalloc; a failure is retried by that call.
+    if (!noalloc_scratch(o->device)) cudaGetLastError();
     *out = o;
     return GS_OK;
 }
@@ -981,7 +989,7 @@ static __device__ __align__(256) float g_noalloc_scratch[kNaFloats];
 namespace {
 
 // Device address of the fixed array on `device` (which must be current):
-// looked up once per device.
+// looked up once per device, normally by gs_opt_init.
 float *noalloc_scratch(int device)
 {
     if (device < 0 || device >= kNaMaxDevices) return nullptr;

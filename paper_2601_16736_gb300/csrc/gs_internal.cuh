@@ -96,16 +96,54 @@ struct StepArgs {
 
 // ------------------------------------------------------- device helpers
 
-// Frustum test of one mean in FP32 with the exact rounding sequence the
-// ABI documents: each product rounded, sums left to right, no FMA.
+// Frustum test of one mean (z_near <= p_z <= z_far, |p_x| <= p_z tan_x,
+// |p_y| <= p_z tan_y with p = R mu + t), decided exactly.
+//
+// Fast path: FP32 with each product rounded and the sums taken left to right.
+// By the inner-product error bound (Higham, Accuracy and Stability of
+// Numerical Algorithms, Sec. 3.1) each computed coordinate is within
+// gamma_4 * S of the exact one, S = sum_j |R_rj mu_j| + |t_r|, and the side
+// test's product p_z tan rounds once more.  Wherever the FP32 slack to every
+// plane exceeds twice that error bound (2^-21 S >= 2 gamma_4 S; 2^-22 of
+// p_z tan for the extra rounding), the FP32 decision is the exact one.  A
+// mean inside the band (a few in a million for scenes of this extent) is
+// decided again in FP64: the products of FP32 values are exact there and the
+// sums round at 2^-53, so the decision is exact up to ~1e-14 of a plane.
+static __device__ __noinline__ bool frustum_visible_f64(float x, float y, float z, float c0, float c1, float c2,
+                                                 float c3, float c4, float c5, float c6, float c7, float c8,
+                                                 float t0, float t1, float t2, float tx, float ty, float zn,
+                                                 float zf)
+{
+    const double X = x, Y = y, Z = z;
+    const double px = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(c0, X), __dmul_rn(c1, Y)), __dmul_rn(c2, Z)), t0);
+    const double py = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(c3, X), __dmul_rn(c4, Y)), __dmul_rn(c5, Z)), t1);
+    const double pz = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(c6, X), __dmul_rn(c7, Y)), __dmul_rn(c8, Z)), t2);
+    return (pz >= (double)zn) && (pz <= (double)zf) && (fabs(px) <= __dmul_rn(pz, (double)tx)) &&
+           (fabs(py) <= __dmul_rn(pz, (double)ty));
+}
+
 __device__ __forceinline__ bool frustum_visible(float x, float y, float z, const float *c)
 {
-    const float px = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[0], x), __fmul_rn(c[1], y)), __fmul_rn(c[2], z)), c[9]);
-    const float py = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[3], x), __fmul_rn(c[4], y)), __fmul_rn(c[5], z)), c[10]);
-    const float pz = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[6], x), __fmul_rn(c[7], y)), __fmul_rn(c[8], z)), c[11]);
+    const float ax = __fmul_rn(c[0], x), bx = __fmul_rn(c[1], y), cx = __fmul_rn(c[2], z);
+    const float ay = __fmul_rn(c[3], x), by = __fmul_rn(c[4], y), cy = __fmul_rn(c[5], z);
+    const float az = __fmul_rn(c[6], x), bz = __fmul_rn(c[7], y), cz = __fmul_rn(c[8], z);
+    const float px = __fadd_rn(__fadd_rn(__fadd_rn(ax, bx), cx), c[9]);
+    const float py = __fadd_rn(__fadd_rn(__fadd_rn(ay, by), cy), c[10]);
+    const float pz = __fadd_rn(__fadd_rn(__fadd_rn(az, bz), cz), c[11]);
     const float wx = __fmul_rn(pz, c[12]);
     const float wy = __fmul_rn(pz, c[13]);
-    return (pz >= c[14]) && (pz <= c[15]) && (fabsf(px) <= wx) && (fabsf(py) <= wy);
+    const bool vis = (pz >= c[14]) && (pz <= c[15]) && (fabsf(px) <= wx) && (fabsf(py) <= wy);
+    // twice the bound on the FP32 evaluation's error, per plane
+    constexpr float k2g4 = 0x1p-21f, k2u = 0x1p-22f;
+    const float ex = k2g4 * (fabsf(ax) + fabsf(bx) + fabsf(cx) + fabsf(c[9]));
+    const float ey = k2g4 * (fabsf(ay) + fabsf(by) + fabsf(cy) + fabsf(c[10]));
+    const float ez = k2g4 * (fabsf(az) + fabsf(bz) + fabsf(cz) + fabsf(c[11]));
+    const bool near_plane = (fabsf(pz - c[14]) <= ez) || (fabsf(c[15] - pz) <= ez) ||
+                            (fabsf(wx - fabsf(px)) <= ex + c[12] * ez + k2u * fabsf(wx)) ||
+                            (fabsf(wy - fabsf(py)) <= ey + c[13] * ez + k2u * fabsf(wy));
+    if (!near_plane) return vis;
+    return frustum_visible_f64(x, y, z, c[0], c[1], c[2], c[3], c[4], c[5], c[6], c[7], c[8], c[9], c[10], c[11],
+                               c[12], c[13], c[14], c[15]);
 }
 
 // SplitMix64 (Steele, Lea & Flood 2014), counter-based: output number

@@ -60,6 +60,27 @@ __device__ __forceinline__ uint32_t pack_bf16x2_sr(float x, float y, uint32_t h)
     return bf16_bits_sr(x, h) | (bf16_bits_sr(y, h >> 16) << 16);
 }
 
+// kW values as BF16 at p, rounded stochastically: one counter hash of (seed,
+// iteration, row, first column) per 4 values, 16 random bits per value.
+// col0 is the state slot of x[0], so every stored value draws its own bits.
+template <int kW>
+__device__ __forceinline__ void store_bf16_sr(char *p, const float *x, const StepArgs &a, int32_t r, int col0)
+{
+    uint32_t w[kW / 2];
+#pragma unroll
+    for (int q = 0; q < kW / 2; q += 2) {
+        const uint32_t h = fmix32((uint32_t)r * 0x9e3779b1u ^ (uint32_t)(col0 + 2 * q) * 0x85ebca77u ^
+                                  (uint32_t)a.k_ctr * 0xc2b2ae3du ^ (uint32_t)a.seed);
+        const uint32_t h2 = fmix32(h ^ 0x27d4eb2fu);
+        w[q] = pack_bf16x2_sr(x[2 * q], x[2 * q + 1], h);
+        w[q + 1] = pack_bf16x2_sr(x[2 * q + 2], x[2 * q + 3], h2);
+    }
+    if (kW == 4)
+        __stcs(reinterpret_cast<uint2 *>(p), make_uint2(w[0], w[1]));
+    else
+        __stcs(reinterpret_cast<uint4 *>(p), make_uint4(w[0], w[1], w[kW > 4 ? 2 : 0], w[kW > 4 ? 3 : 0]));
+}
+
 // ------------------------------------------------------------ state formats
 // A small chunk (small item c = 12, 13, 14): 4 moments of m and of v as FP32,
 // plus t where the format keeps it in chunk 14.
@@ -150,7 +171,9 @@ __device__ __forceinline__ void store_bf16_rn(char *p, const float *x)
 
 // BF16 rows of 64 slots (128 B): SH column j at byte 2j; small chunk c at byte
 // 8c; t = uint32 at byte 120, loaded and stored with chunk 14 as one 16-B
-// access (slots 56-63).
+// access (slots 56-63).  m is rounded to nearest; v is rounded
+// stochastically (its ~0.1 % per-step EMA increment is below BF16's
+// resolution, and round-to-nearest would freeze it).
 template <>
 struct State<GS_MOM_BF16> {
     static constexpr int kRowBytes = kRowBytesBf16, kTByte = kTByteBf16;
@@ -170,7 +193,7 @@ struct State<GS_MOM_BF16> {
                                                     const float *v, uint32_t)
     {
         store_bf16_rn<kW>(row(a.m, r) + 2 * kW * i, m);
-        store_bf16_rn<kW>(row(a.v, r) + 2 * kW * i, v);
+        store_bf16_sr<kW>(row(a.v, r) + 2 * kW * i, v, a, r, kW * i);
     }
     static __device__ __forceinline__ Chunk load_small(const StepArgs &a, int32_t r, int c)
     {
@@ -199,8 +222,8 @@ struct State<GS_MOM_BF16> {
             __stcs(reinterpret_cast<uint4 *>(row(a.m, r) + 112),
                    make_uint4(pack_bf16x2(k.m.x, k.m.y), pack_bf16x2(k.m.z, k.m.w), k.t, 0u));
         }
-        __stcs(reinterpret_cast<uint2 *>(row(a.v, r) + 8 * c),
-               make_uint2(pack_bf16x2(k.v.x, k.v.y), pack_bf16x2(k.v.z, k.v.w)));
+        const float vv[4] = {k.v.x, k.v.y, k.v.z, k.v.w};
+        store_bf16_sr<4>(row(a.v, r) + 8 * c, vv, a, r, 4 * c);
     }
 };
 
@@ -248,20 +271,7 @@ struct State<GS_MOM_BF16_HYBRID> {
             mm[0] = mm[1] = mm[2] = vv[0] = vv[1] = vv[2] = 0.f;   // BF16 DC slots are unused
         }
         store_bf16_rn<kW>(row(a.m, r) + kHybShByte + 2 * kW * i, mm);
-        uint32_t w[kW / 2];
-#pragma unroll
-        for (int q = 0; q < kW / 2; q += 2) {
-            const uint32_t h = fmix32((uint32_t)r * 0x9e3779b1u ^ (uint32_t)(kW * i + 2 * q) * 0x85ebca77u ^
-                                      (uint32_t)a.k_ctr * 0xc2b2ae3du ^ (uint32_t)a.seed);
-            const uint32_t h2 = fmix32(h ^ 0x27d4eb2fu);
-            w[q] = pack_bf16x2_sr(vv[2 * q], vv[2 * q + 1], h);
-            w[q + 1] = pack_bf16x2_sr(vv[2 * q + 2], vv[2 * q + 3], h2);
-        }
-        char *pv = row(a.v, r) + kHybShByte + 2 * kW * i;
-        if (kW == 4)
-            __stcs(reinterpret_cast<uint2 *>(pv), make_uint2(w[0], w[1]));
-        else
-            __stcs(reinterpret_cast<uint4 *>(pv), make_uint4(w[0], w[1], w[kW > 4 ? 2 : 0], w[kW > 4 ? 3 : 0]));
+        store_bf16_sr<kW>(row(a.v, r) + kHybShByte + 2 * kW * i, vv, a, r, kW * i);
     }
     static __device__ __forceinline__ Chunk load_small(const StepArgs &a, int32_t r, int c)
     {

@@ -104,11 +104,44 @@ class OracleRun:
         self.row_ids = None if row_ids is None else np.asarray(row_ids, np.int64)
 
     def visible(self, cam16) -> np.ndarray:
-        """FP32 frustum decision on the oracle's own positions rounded to FP32."""
+        """The oracle's (FP64) frustum decision on its own positions rounded
+        to FP32."""
         xyz32 = self.st.theta[:, 0:3].astype(np.float32)
-        return self.orc.visibility_f32(xyz32, cam16)
+        return self.orc.visibility(xyz32, cam16)
 
     def step(self, grad_rows, mask, lr, dar_o, dar_s, k, restate=False, ratio=0.0, seed=0, n_visible=0):
         self.orc.step(self.cfg, self.st, grad_rows, mask, lr, dar_o, dar_s, k, n_visible)
         if restate:
             self.orc.restate(self.cfg, self.st, seed, k, ratio, row_ids=self.row_ids)
+
+
+# Rows within this distance of a frustum plane may be decided either way
+# (the tolerance the visibility parity is stated with).
+PLANE_TOL = 1e-6
+
+
+def check_mask(orc, got, xyz, cam16) -> dict:
+    """The GPU mask `got` against the oracle's FP64 decision on the same FP32
+    means: every disagreement must lie within PLANE_TOL of a plane.  Returns
+    the rows within PLANE_TOL of a plane and the disagreements among them."""
+    margin, ref = orc.frustum_margin_f64(xyz, cam16)
+    differ = np.asarray(got, np.uint8) != ref
+    near = np.abs(margin) <= PLANE_TOL
+    bad = differ & ~near
+    assert not bad.any(), (f"{int(bad.sum())} visibility decisions differ from the FP64 definition away from "
+                           f"the planes (largest |margin| {np.abs(margin[bad]).max():.3e})")
+    return {"near_plane": int(near.sum()), "differ": int(differ.sum())}
+
+
+def check_trajectory_masks(orc, gmask, omask, orc_xyz, gpu_xyz, cam16) -> int:
+    """Masks of the same step taken on the GPU's and the oracle's positions,
+    which differ by the FP32 rounding of earlier steps.  The GPU decides
+    exactly, so a decision may differ only where the oracle's mean is within
+    |mu_gpu - mu_oracle| + PLANE_TOL of a plane (R is a rotation, so moving a
+    mean by d moves its plane distances by at most |d|).  Returns the count."""
+    differ = np.asarray(gmask, np.uint8) != np.asarray(omask, np.uint8)
+    if differ.any():
+        margin, _ = orc.frustum_margin_f64(np.asarray(orc_xyz, np.float32)[differ], cam16)
+        d = np.linalg.norm(np.asarray(gpu_xyz, np.float64)[differ] - np.asarray(orc_xyz, np.float64)[differ], axis=1)
+        assert np.all(np.abs(margin) <= d + PLANE_TOL), "decision differs farther from a plane than the means do"
+    return int(differ.sum())

@@ -71,6 +71,11 @@ def test_batch_equals_single_scene_steps(G, prec):
 
 
 def test_batch_matches_oracle(G, orc):
+    """Two scenes in one batched launch against the oracle: 1e-5 after the
+    first step, 1e-4 after 300 steps with RSR every 100.  Rows whose mean
+    came within 1e-5 of a frustum plane at some step are left out of the
+    300-step comparison: there the GPU (deciding on its FP32 means) and the
+    oracle (on its FP64 means rounded to FP32) may see different sides."""
     sizes = [3_001, 20_011]
     runs, refs, cams = [], [], []
     for i, n in enumerate(sizes):
@@ -78,20 +83,32 @@ def test_batch_matches_oracle(G, orc):
         runs.append(GpuScene(groups))
         refs.append(OracleRun(orc, synth.to_rows(groups)))
         cams.append(synth.ring_cameras(6, (0.0, 30.0)))
+    near = [np.zeros(n, bool) for n in sizes]
     b = G.gs_batch_create([r.h for r in runs])
-    for k in range(1, 21):
+    steps = 300
+    for k in range(1, steps + 1):
         for s, (r, ref) in enumerate(zip(runs, refs)):
-            g = synth.grads_rows(sizes[s], 1500 + s, k)
+            g = synth.grads_rows(sizes[s], 1500 + s, k % 7)
             r.set_grads(g)
-            lr = synth.lr_for_step(k, 20)
+            lr = synth.lr_for_step(k, steps)
             cam = cams[s][k % len(cams[s])]
+            rs = k % 100 == 0
             b.set(s, G.make_attrs(r.attrs), G.make_attrs(r.grads), G.make_camera(cam),
-                  G.make_params(lr, k, restate=(k == 10), restate_ratio=0.5, seed=7))
-            ref.step(g, ref.visible(cam), lr, True, True, k, restate=(k == 10), ratio=0.5, seed=7)
+                  G.make_params(lr, k, restate=rs, restate_ratio=0.5, seed=7))
+            margin, vis = orc.frustum_margin_f64(ref.st.theta[:, 0:3].astype(np.float32), cam)
+            near[s] |= np.abs(margin) < 1e-5
+            ref.step(g, vis, lr, True, True, k, restate=rs, ratio=0.5, seed=7)
         G.gs_batch_step(b)
         torch.cuda.synchronize()
-    for r, ref in zip(runs, refs):
-        assert_close(r.rows(), ref.st.theta, 1e-4, what="batched scene")
+        if k == 1:
+            for r, ref in zip(runs, refs):
+                assert_close(r.rows(), ref.st.theta, 1e-5, 1e-5, what="batched scene, step 1")
+    for s, (r, ref) in enumerate(zip(runs, refs)):
+        keep = ~near[s]
+        assert keep.mean() > 0.99
+        assert_close(r.rows(), ref.st.theta, 1e-4, rows=keep, what=f"batched scene, {steps} steps")
+        _, _, t = r.state()
+        assert np.array_equal(t[keep], ref.st.t[keep])
     b.close()
     for r in runs:
         r.close()

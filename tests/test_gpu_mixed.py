@@ -6,15 +6,16 @@ Bounds, from the arithmetic: the step computes every moment in FP32 and only
 rounds the stored copy, so after one step from zero state the attributes are
 as accurate as the FP32 path and each stored moment is within BF16's rounding
 of the oracle's: half an ulp (2^-8 relative) when rounded to nearest, one ulp
-(2^-7) when rounded stochastically (the hybrid's SH second moments).  For
+(2^-7) when rounded stochastically (the second moments of BF16 columns).  For
 FP16 blocks the ulp is 2^-10 relative for every value within 2^29 of its
 group's largest magnitude; below that FP16 subnormals space values 2^-24
 apart in the group's scaled units.  Over
 many steps the rounded moments feed back; after 1000 steps of the 3 M
 workload the metric's gate, group relative L2 ||d|| / ||theta_ref|| <= 1e-3,
-is asserted for the hybrid.  All-BF16 misses it (its second moments move
-~0.1 % per step, below BF16 resolution; opacity ends near 1e-2); its test
-bound 3e-2 only guards against regressions.
+is asserted for FP16 block and the hybrid.  All-BF16 and FP8 miss it (8 and 4
+significant bits cannot carry a second moment that moves ~0.1 % per step, nor
+the first moments of the opacity and SH-DC columns); they are held to a
+recorded regression bound and reported as failing the gate.
 """
 import numpy as np
 import pytest
@@ -107,7 +108,7 @@ def test_one_step(G, orc, prec):
     vis = ref.visible(cam)
     ref.step(grads, vis, LR, True, True, 100, restate=True, ratio=0.3, seed=9)
     assert_close(got, ref.st.theta, 1e-5, 1e-5, what="theta")
-    v_ulps = 1.0 if prec == "BF16" else 2.0              # stochastic rounding: within one ulp
+    v_ulps = 2.0                                         # stochastic rounding: within one ulp
     half = FP16_HALF_ULP if prec == "FP16_BLOCK" else BF16_HALF_ULP
     for name, a, b, ulps in [("m", m, ref.st.m, 1.0), ("v", v, ref.st.v, v_ulps)]:
         d = np.abs(a - b)
@@ -197,24 +198,29 @@ def _run_sampled(G, orc, wl, prec, sample):
     return got, ref.st.theta, ~diverged
 
 
-@pytest.mark.parametrize("prec,gate", [("FP16_BLOCK", 1e-3), ("BF16_HYBRID", 1e-3), ("BF16", 3e-2),
-                                       ("FP8E4M3", None)])
-def test_3m_1000_steps_sampled(G, orc, prec, gate):
+# (format, meets the 1e-3 gate, regression bound on the largest group error)
+MIXED_3M = [("FP16_BLOCK", True, 1e-3), ("BF16_HYBRID", True, 1e-3), ("BF16", False, 3e-2),
+            ("FP8E4M3", False, 0.1)]
+
+
+@pytest.mark.parametrize("prec,meets_gate,bound", MIXED_3M)
+def test_3m_1000_steps_sampled(G, orc, prec, meets_gate, bound):
     """The 3 M-primitive, 1000-step workload (about 20 % visible per view),
-    followed by the oracle on 2000 sampled primitives.  FP8 (e4m3, 3 mantissa
-    bits) has no gate: its errors are recorded and pinned only to stay
-    finite and below 1 (no blow-up from a second moment stored as zero)."""
+    followed by the oracle on 2000 sampled primitives.  The formats that
+    meet the 1e-3 gate are asserted against it; the others are held to a
+    recorded regression bound and then marked as failing the gate (xfail,
+    with the measured error), which is not a pass."""
     wl = synth.WORKLOADS["c3_3m"]
     sample = np.sort(np.random.default_rng(17).choice(wl.n, 2000, replace=False))
     got, ref, keep = _run_sampled(G, orc, wl, prec, sample)
-    assert keep.mean() > (0.9 if gate is None else 0.998)
+    assert keep.mean() > (0.998 if meets_gate else 0.9)
     errs = group_rel_l2(got, ref, rows=keep)
+    worst = max(errs.values())
     print(prec, "group relative L2 after 1000 steps:", errs)
     for g, e in errs.items():
-        if gate is None:
-            assert np.isfinite(e) and e < 1.0, f"{prec} group {g}: {e:.2e}"
-        else:
-            assert e <= gate, f"{prec} group {g}: {e:.2e} > {gate:.0e}"
+        assert np.isfinite(e) and e <= bound, f"{prec} group {g}: {e:.2e} > {bound:.0e}"
+    if not meets_gate:
+        pytest.xfail(f"{prec}: largest group error {worst:.2e} after 1000 steps, above the 1e-3 gate")
 
 
 def test_fp16_block_with_optional_terms(G, orc):

@@ -9,7 +9,7 @@ compared bit-exactly.
 import numpy as np
 import pytest
 
-from harness import GpuScene, OracleRun, assert_close, group_errors
+from harness import check_mask, check_trajectory_masks, GpuScene, OracleRun, assert_close, group_errors
 from paper_2601_16736_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -32,7 +32,10 @@ def G():
 # ------------------------------------------------------------- visibility
 
 @pytest.mark.parametrize("scene", ["uniform", "blobs"])
-def test_visibility_bit_exact(G, orc, scene):
+def test_visibility_matches_fp64_definition(G, orc, scene):
+    """Mask, count and list against the oracle's FP64 frustum decision: equal
+    everywhere except means within 1e-6 of a plane, which are counted and
+    reported with the disagreements among them."""
     n = 250_001
     groups = synth.scene_uniform(n, 91) if scene == "uniform" else synth.scene_blobs(n, 92, 12.5)
     xyz = torch.from_numpy(groups["xyz"]).cuda()
@@ -40,23 +43,70 @@ def test_visibility_bit_exact(G, orc, scene):
     mask = torch.zeros(n, dtype=torch.uint8, device="cuda")
     rows = torch.full((n,), -1, dtype=torch.int32, device="cuda")
     cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
-    near = 0
+    near = differ = 0
     for cam in synth.ring_cameras(6, (-30.0, 0.0, 30.0)):
         G.gs_visibility(run.h, xyz, G.make_camera(cam), mask, rows, cnt)
         torch.cuda.synchronize()
-        ref = orc.visibility_f32(groups["xyz"], cam)
         got = mask.cpu().numpy()
-        assert np.array_equal(got, ref)
-        c = int(cnt.item())
-        assert c == int(ref.sum())
-        lst = rows.cpu().numpy()[:c]
-        assert np.array_equal(np.sort(lst), np.nonzero(ref)[0])
-        margin, mask64 = orc.frustum_margin_f64(groups["xyz"], cam)
-        near += int((np.abs(margin) < 1e-6).sum())
-        differ = mask64 != ref
-        assert np.all(np.abs(margin[differ]) < 1e-4), "FP32/FP64 decisions differ away from the planes"
-    print(f"rows within 1e-6 of a frustum plane (all views): {near}")
+        c = check_mask(orc, got, groups["xyz"], cam)
+        near += c["near_plane"]
+        differ += c["differ"]
+        assert int(cnt.item()) == int(got.sum())
+        lst = rows.cpu().numpy()[:int(cnt.item())]
+        assert np.array_equal(np.sort(lst), np.nonzero(got)[0])
+    print(f"means within 1e-6 of a frustum plane: {near}; decisions differing from FP64: {differ}")
+    assert differ == 0
     run.close()
+
+
+def _near_plane_means(cam, n, seed):
+    """Means placed at relative distances 1e-8 .. 1e-4 from the side planes
+    of `cam` (margins of about 1e-8 .. 1e-3): most fall inside the FP32
+    evaluation's rounding band, where the kernels decide in FP64."""
+    rng = np.random.default_rng(seed)
+    R = cam[:9].reshape(3, 3).astype(np.float64)
+    t = cam[9:12].astype(np.float64)
+    tx, ty = float(cam[12]), float(cam[13])
+    pz = rng.uniform(0.5, 40.0, n)
+    side = rng.integers(0, 4, n)
+    d = rng.normal(0, 1, n) * 10.0 ** rng.uniform(-8, -4, n)
+    sgn = np.where(side % 2 == 0, 1.0, -1.0)
+    px = np.where(side < 2, sgn * pz * tx * (1 + d), rng.uniform(-1, 1, n) * pz * tx)
+    py = np.where(side >= 2, sgn * pz * ty * (1 + d), rng.uniform(-1, 1, n) * pz * ty)
+    return ((np.stack([px, py, pz], 1) - t) @ R).astype(np.float32)
+
+
+def test_visibility_exact_near_planes(G, orc):
+    """Means inside the FP32 rounding band of the side planes: the GPU's
+    decision (FP32, re-taken in FP64 inside twice the FP32 error bound)
+    equals the FP64 definition away from 1e-6 of a plane, and in fact
+    everywhere but within 1e-9 of one.  A plain FP32 evaluation differs from
+    FP64 on thousands of these rows, many of them farther than 1e-6 from the
+    plane."""
+    n = 200_003
+    tot = {"near_plane": 0, "differ": 0, "differ_beyond_1e-9": 0, "fp32_differ_beyond_1e-6": 0}
+    for i, cam in enumerate(synth.ring_cameras(4, (-30.0, 0.0, 30.0))):
+        xyz_np = _near_plane_means(cam, n, 1200 + i)
+        run = GpuScene({"xyz": xyz_np, "scale": np.zeros((n, 3), np.float32), "rot": np.zeros((n, 4), np.float32),
+                        "opacity": np.zeros((n, 1), np.float32), "sh": np.zeros((n, 48), np.float32)})
+        mask = torch.zeros(n, dtype=torch.uint8, device="cuda")
+        G.gs_visibility(run.h, run.attrs["xyz"], G.make_camera(cam), mask)
+        got = mask.cpu().numpy()
+        c = check_mask(orc, got, xyz_np, cam)
+        margin, ref = orc.frustum_margin_f64(xyz_np, cam)
+        tot["near_plane"] += c["near_plane"]
+        tot["differ"] += c["differ"]
+        tot["differ_beyond_1e-9"] += int(((got != ref) & (np.abs(margin) > 1e-9)).sum())
+        f32 = orc.visibility_f32(xyz_np, cam)
+        tot["fp32_differ_beyond_1e-6"] += int(((f32 != ref) & (np.abs(margin) > 1e-6)).sum())
+        # the fused step takes the same decision
+        run.step_camera(cam, G.make_params(LR, 1))
+        torch.cuda.synchronize()
+        assert np.array_equal(run.mask[:n].cpu().numpy(), got)
+        run.close()
+    print("near-plane means:", tot)
+    assert tot["differ_beyond_1e-9"] == 0
+    assert tot["fp32_differ_beyond_1e-6"] > 0, "the probe does not reach the FP32 rounding band"
 
 
 def _runs_ascending(lst, tile):
@@ -86,8 +136,8 @@ def test_visibility_layouts_and_list_order(G, orc, offset):
     for cam in synth.ring_cameras(4):
         G.gs_visibility(run.h, xyz, G.make_camera(cam), mask, rows, cnt)
         torch.cuda.synchronize()
-        ref = orc.visibility_f32(groups["xyz"][offset:], cam)
-        assert np.array_equal(mask.cpu().numpy(), ref)
+        ref = mask.cpu().numpy()
+        check_mask(orc, ref, groups["xyz"][offset:], cam)
         c = int(cnt.item())
         assert c == int(ref.sum())
         lst = rows.cpu().numpy()[:c]
@@ -222,6 +272,7 @@ def _run_sequence(G, orc, wl, n_steps, sample=None):
     ref = OracleRun(orc, synth.to_rows(groups)[ids], row_ids=ids)
     diverged = np.zeros(ids.size, bool)
     n_ambiguous = 0
+    ids_dev = torch.from_numpy(ids).cuda()
     for k in range(1, n_steps + 1):
         cam = cams[order[k - 1]]
         b = (k - 1) % nbuf
@@ -229,15 +280,14 @@ def _run_sequence(G, orc, wl, n_steps, sample=None):
         rs = k % wl.restate_every == 0
         p = G.make_params(lr, k, dar_opacity=wl.dar, dar_scale=wl.dar, restate=rs,
                           restate_ratio=wl.restate_ratio, seed=wl.seed)
+        gxyz = run.attrs["xyz"][ids_dev].cpu().numpy()          # the means this step decides on
         G.gs_step_camera(run.h, G.make_attrs(run.attrs), G.make_attrs(gdev[b]), G.make_camera(cam), p,
                          mask_out=run.mask)
-        gmask = run.mask[torch.from_numpy(ids).cuda()].cpu().numpy() if sample is not None else run.mask.cpu().numpy()
+        gmask = run.mask[ids_dev].cpu().numpy()
         omask = ref.visible(cam)
         differ = gmask != omask
         if differ.any():
-            margin, _ = orc.frustum_margin_f64(ref.st.theta[differ, 0:3].astype(np.float32), cam)
-            assert np.all(np.abs(margin) < 1e-4), "decision differs away from a frustum plane"
-            n_ambiguous += int(differ.sum())
+            n_ambiguous += check_trajectory_masks(orc, gmask, omask, ref.st.theta[:, 0:3], gxyz, cam)
             diverged |= differ
         ref.step(grads_host[b][ids], omask, lr, wl.dar, wl.dar, k,
                  restate=rs, ratio=wl.restate_ratio, seed=wl.seed)
