@@ -333,6 +333,26 @@ __device__ __forceinline__ float2 factors(const StepArgs &a, uint32_t k)
     return k < (uint32_t)a.fac_len ? a.fac[k] : make_float2(1.0f, 1.0f);
 }
 
+// Beside the means: ask L2 for what phase A of the tile one wave ahead reads
+// for its rows, so that its loads find them on chip: the opacity logits when
+// counting N_a or drawing noise, and the rotations and log-scales for noise.
+// A hint only; whole tiles, 16-B aligned sources.
+template <int kTile>
+__device__ __forceinline__ void prefetch_tile_ahead_x(const StepArgs &a)
+{
+    if (threadIdx.x != 0 || a.tile_ahead <= 0 || !(a.n_active || a.noise)) return;
+    const int64_t q = ((int64_t)blockIdx.x + a.tile_ahead) * kTile;
+    if (q + kTile > (int64_t)a.n_rows) return;
+    if (((uintptr_t)a.a_op & 15u) == 0)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.a_op + q), "n"(kTile * 4) : "memory");
+    if (a.noise) {
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.a_rot + q * 4), "n"(kTile * 16) : "memory");
+        if (((uintptr_t)a.a_scale & 15u) == 0)
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.a_scale + q * 3), "n"(kTile * 12)
+                         : "memory");
+    }
+}
+
 // Phase A of the extended step; returns the two list lengths.
 template <int kTile, int kRowBytes, int kTByte>
 __device__ __forceinline__ void tile_decide_x(const StepArgs &a, const int vis_src, const int64_t r0,
@@ -446,6 +466,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) step_tile_x(const StepAr
     constexpr int kNsh = 48 / kW;
     __shared__ TileListsX<kTile> L;
     prefetch_tile_ahead<kTile>(a, vis_src);
+    prefetch_tile_ahead_x<kTile>(a);
     const int64_t r0 = (int64_t)blockIdx.x * kTile;
     int nv, ni;
     tile_decide_x<kTile, S::kRowBytes, S::kTByte>(a, vis_src, r0, L, nv, ni);
@@ -453,25 +474,30 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) step_tile_x(const StepAr
     unsigned my_active = 0;
     constexpr int kSmall = kSmallItems<kPrec>, kOpItem = 11 + kSmall;     // the item holding the opacity
     const int e_sh = kNsh * nv, e_vis = e_sh + kSmall * nv, e_ish = e_vis + kNsh * ni, e_all = e_ish + kSmall * ni;
-    for (int w = threadIdx.x; w < e_all; w += kThreads) {
-        if (w < e_sh) {
-            const int j = w / kNsh, i = w - j * kNsh;
-            sh_item<kPrec, kW>(a, L.list[j], i, (L.vflag[j] & kFRsr) != 0, L.fac[j]);
-        } else if (w < e_vis) {
-            const int q = w - e_sh;
-            const int j = q % nv, c = 12 + q / nv;
-            const bool act = small_item_x<kPrec>(a, L.list[j], c, true, L.vflag[j], L.fac[j], L.nz[j]);
-            my_active += (c == kOpItem && act) ? 1u : 0u;
-        } else if (w < e_ish) {
-            const int q = w - e_vis;
-            const int j = q / kNsh, i = q - j * kNsh;
-            inv_sh_item<kPrec, kW>(a, L.ilist[j], i, L.iflag[j], L.ifac[j]);
-        } else {
-            const int q = w - e_ish;
-            const int j = q % ni, c = 12 + q / ni;
-            const bool act = small_item_x<kPrec>(a, L.ilist[j], c, false, L.iflag[j], L.ifac[j], L.inz[j]);
-            my_active += (c == kOpItem && act) ? 1u : 0u;
-        }
+    // One flat item space walked as four loops, one per item kind, with the
+    // item-to-thread assignment a single loop would give: the kinds do not
+    // share a loop body, so their register demands do not add up.
+    int w = threadIdx.x;
+    for (; w < e_sh; w += kThreads) {
+        const int j = w / kNsh, i = w - j * kNsh;
+        sh_item<kPrec, kW>(a, L.list[j], i, (L.vflag[j] & kFRsr) != 0, L.fac[j]);
+    }
+    for (; w < e_vis; w += kThreads) {
+        const int q = w - e_sh;
+        const int j = q % nv, c = 12 + q / nv;
+        const bool act = small_item_x<kPrec>(a, L.list[j], c, true, L.vflag[j], L.fac[j], L.nz[j]);
+        my_active += (c == kOpItem && act) ? 1u : 0u;
+    }
+    for (; w < e_ish; w += kThreads) {
+        const int q = w - e_vis;
+        const int j = q / kNsh, i = q - j * kNsh;
+        inv_sh_item<kPrec, kW>(a, L.ilist[j], i, L.iflag[j], L.ifac[j]);
+    }
+    for (; w < e_all; w += kThreads) {
+        const int q = w - e_ish;
+        const int j = q % ni, c = 12 + q / ni;
+        const bool act = small_item_x<kPrec>(a, L.ilist[j], c, false, L.iflag[j], L.ifac[j], L.inz[j]);
+        my_active += (c == kOpItem && act) ? 1u : 0u;
     }
     if (a.n_active) {
         my_active = __reduce_add_sync(0xffffffffu, my_active);
@@ -484,10 +510,11 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) step_tile_x(const StepAr
 }  // namespace
 
 constexpr int kExtTile = 256;
-// Resident CTAs per SM: 5 for FP32 moments (48 registers, no spills), 4 for
-// the other formats (5 would spill).
+// Resident CTAs per SM: 5 for FP32 and BF16 moments (48 registers, no
+// spills; BF16 4 % faster than at 4), 4 for the hybrid and FP16-block
+// formats (at 5 they spill and gain nothing).
 template <int kPrec>
-constexpr int kExtMinBlocks = kPrec == GS_MOM_FP32 ? 5 : 4;
+constexpr int kExtMinBlocks = (kPrec == GS_MOM_FP32 || kPrec == GS_MOM_BF16) ? 5 : 4;
 
 namespace {
 
