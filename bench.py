@@ -430,10 +430,13 @@ def run_ours(args):
     if rank == 0 and args.mixed:
         # the gate-passing 16-bit format on the headline workload itself
         rf = timed_run(G, sc, "fp16_block", args.steps, args.warmup)
+        t16, a16, n16 = captured_traffic(wl.name, "fp16_block")
         out["mixed_precision_headline"] = {
             "workload": f"{wl.name} (this line's workload), {args.steps} timed steps",
             "fp16_block": {"value": rf["nv"] / rf["elapsed"], "ms_per_step": rf["elapsed"] / args.steps * 1e3,
                            "p50_ms": rf["p50_ms"], "hbm_gbs": rf["bytes_per_launch"] / rf["kern"] / 1e9,
+                           "traffic": t16, "traffic_over_algorithmic": t16 / a16 if t16 else None,
+                           "traffic_source": n16,
                            "speedup_vs_fp32": (rf["nv"] / rf["elapsed"]) / (r["nv"] / r["elapsed"]),
                            "error": error_vs_fp32(G, sc, "fp16_block") if args.mixed_error else None}}
     if rank == 0 and e2e_steps > 0:
