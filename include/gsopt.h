@@ -156,9 +156,12 @@ typedef struct gs_opt_config {
 
 /* Pinhole camera of the current view: p = R mu + t (R row-major,
  * world -> camera, camera looking down +z).  A mean is visible iff
- * z_near <= p.z <= z_far, |p.x| <= p.z tan_half_fovx, |p.y| <= p.z tan_half_fovy,
- * evaluated in FP32 with every product rounded before it is summed, sums taken
- * left to right ((R0 mu0 + R1 mu1) + R2 mu2) + t0, and no fused multiply-add. */
+ * z_near <= p.z <= z_far, |p.x| <= p.z tan_half_fovx, |p.y| <= p.z tan_half_fovy
+ * (Eq. meth::sparse_beta's V, read as the frustum test of the mean), decided
+ * exactly for the given FP32 values: the test is evaluated in FP32 and taken
+ * again in FP64 for every mean within twice the FP32 evaluation's rounding
+ * bound of a plane, so the decision can differ from exact arithmetic only
+ * within ~1e-14 (relative to the coordinates) of a plane. */
 typedef struct gs_camera {
     float R[9];
     float t[3];
