@@ -22,6 +22,7 @@ from __future__ import annotations
 
 import argparse
 import ctypes
+import dataclasses
 import json
 import os
 import subprocess
@@ -389,6 +390,8 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     wl = synth.WORKLOADS[args.workload]
+    if args.grad_buffers:
+        wl = dataclasses.replace(wl, grad_buffers=args.grad_buffers)
     seed = replica_seed(wl.seed, rank)
     e2e_steps = args.e2e_steps if args.e2e_steps is not None else args.steps
     k0, n_scene = headline_plan(args.warmup, args.steps, e2e_steps, wl.restate_every)
@@ -1011,9 +1014,17 @@ def main():
     ap.add_argument("--no-secondary", dest="secondary", action="store_false",
                     help="skip the blob-sorted row order and the 100 k (L2-resident) legs")
     ap.add_argument("--no-visibility-band", dest="visibility_band", action="store_false")
+    ap.add_argument("--only", choices=["mixed", "batched", "reindex", "next_rows", "ceiling"], default=None,
+                    help="run the headline and this one leg only (for profiling)")
+    ap.add_argument("--grad-buffers", type=int, default=None,
+                    help="gradient buffers per scene (default: the workload's pool); fewer keeps profiled runs small")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.only:
+        for leg in ("mixed", "batched", "reindex", "next_rows", "ceiling", "secondary", "cpu_baseline"):
+            setattr(args, leg, leg == args.only)
+        args.e2e_steps = 0
     if args.impl == "reference":
         run_reference(args)
     elif args.density_sweep:

@@ -441,9 +441,11 @@ gs_status gs_visibility(gs_opt *o, const float *xyz, const gs_camera *cam, uint8
         return GS_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaSuccess;
+    float c[gs::kCamFloats];
+    gs::camera_arg(reinterpret_cast<const float *>(cam), c);
     if (n_visible) e = cudaMemsetAsync(n_visible, 0, 8, s);
     if (e == cudaSuccess)
-        e = gs::launch_visibility(xyz, (int32_t)n, reinterpret_cast<const float *>(cam), mask, visible_rows,
+        e = gs::launch_visibility(xyz, (int32_t)n, c, mask, visible_rows,
                                   reinterpret_cast<unsigned long long *>(n_visible), s);
     return fail_cuda(o, e);
 }
@@ -481,7 +483,7 @@ gs_status gs_step_camera(gs_opt *o, const gs_attrs *attrs, const gs_grads *grads
     StepArgs a;
     fill_args(o, params, &a);
     set_attrs(&a, attrs, grads);
-    memcpy(a.cam, cam, sizeof(a.cam));
+    gs::camera_arg(reinterpret_cast<const float *>(cam), a.cam);
     a.mask_out = mask_out;
     a.n_visible = reinterpret_cast<unsigned long long *>(n_visible);
     return fail_cuda(o, gs::launch_step(a, o->cfg.prec, gs::kVisCamera, s));
@@ -516,7 +518,7 @@ gs_status gs_step_host(gs_opt *o, const gs_attrs *attrs, const gs_grads *gh, con
             StepArgs a;
             fill_args(o, params, &a);
             set_attrs(&a, attrs, &gd);
-            memcpy(a.cam, cam, sizeof(a.cam));
+            gs::camera_arg(reinterpret_cast<const float *>(cam), a.cam);
             a.n_visible = o->count;
             a.g_host = 1;
             cudaError_t e = cudaMemsetAsync(o->count, 0, sizeof(unsigned long long), s);
@@ -564,7 +566,7 @@ gs_status gs_step_host(gs_opt *o, const gs_attrs *attrs, const gs_grads *gh, con
     StepArgs a;
     fill_args(o, params, &a);
     set_attrs(&a, attrs, &gd);
-    memcpy(a.cam, cam, sizeof(a.cam));
+    gs::camera_arg(reinterpret_cast<const float *>(cam), a.cam);
     a.n_visible = o->count;
     if (e == cudaSuccess) e = cudaMemsetAsync(o->count, 0, sizeof(unsigned long long), s);
     if (e == cudaSuccess) e = gs::launch_step(a, o->cfg.prec, gs::kVisCamera, s);
@@ -771,7 +773,7 @@ void batch_fill(gs_batch *b, int cand, const gs_attrs *attrs, const gs_grads *gr
         StepArgs &a = hp->args[s];
         fill_args(o, &params[s], &a);
         set_attrs(&a, &attrs[s], &grads[s]);
-        memcpy(a.cam, &cams[s], sizeof(a.cam));
+        gs::camera_arg(reinterpret_cast<const float *>(&cams[s]), a.cam);
         a.n_visible = n_visible ? reinterpret_cast<unsigned long long *>(n_visible + s) : nullptr;
     }
     hp->tile_start[n] = total;
@@ -1031,7 +1033,7 @@ extern "C" gs_status gs_step_host_noalloc(gs_opt *o, const gs_attrs *attrs, cons
     StepArgs a;
     fill_args(o, params, &a);
     set_attrs(&a, attrs, &gd);
-    memcpy(a.cam, cam, sizeof(a.cam));
+    gs::camera_arg(reinterpret_cast<const float *>(cam), a.cam);
     a.n_visible = count;
     if (e == cudaSuccess) e = gs::launch_step(a, o->cfg.prec, gs::kVisCamera, s);
     unsigned long long h = 0;

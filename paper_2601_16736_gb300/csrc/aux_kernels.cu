@@ -18,11 +18,15 @@ __device__ __forceinline__ void record_error(int32_t *err, int32_t code)
 }
 
 // ---------------------------------------------------------------- visibility
+struct CamArg {
+    float c[kCamFloats];
+};
+
 // One thread per row decides V (frustum test of the mean); each CTA compacts
 // its visible rows with warp ballots, reserves a contiguous range of the
 // output list with one atomicAdd, and writes them in ascending row order.
 __global__ void __launch_bounds__(kThreads) visibility_kernel(const float *__restrict__ xyz, int32_t n,
-                                                              const gs_camera cam, uint8_t *__restrict__ mask,
+                                                              const CamArg cam, uint8_t *__restrict__ mask,
                                                               int32_t *__restrict__ list,
                                                               unsigned long long *__restrict__ count)
 {
@@ -30,7 +34,7 @@ __global__ void __launch_bounds__(kThreads) visibility_kernel(const float *__res
     __shared__ unsigned long long s_base;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t row = (int64_t)blockIdx.x * kThreads + tid;
-    const float *c = reinterpret_cast<const float *>(&cam);
+    const float *c = cam.c;
     bool vis = false;
     if (row < n) {
         const float *p = xyz + row * 3;
@@ -62,7 +66,7 @@ __global__ void __launch_bounds__(kThreads) visibility_kernel(const float *__res
 constexpr int kVisRpt = 4;
 
 __global__ void __launch_bounds__(kThreads) visibility4_kernel(const float *__restrict__ xyz, int32_t n,
-                                                               const gs_camera cam, uint8_t *__restrict__ mask,
+                                                               const CamArg cam, uint8_t *__restrict__ mask,
                                                                int32_t *__restrict__ list,
                                                                unsigned long long *__restrict__ count)
 {
@@ -70,7 +74,7 @@ __global__ void __launch_bounds__(kThreads) visibility4_kernel(const float *__re
     __shared__ unsigned long long s_base;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t r0 = ((int64_t)blockIdx.x * kThreads + tid) * kVisRpt;
-    const float *c = reinterpret_cast<const float *>(&cam);
+    const float *c = cam.c;
     unsigned vis = 0;                      // bit j: row r0 + j is visible
     if (r0 + kVisRpt <= n) {
         const float4 *p = reinterpret_cast<const float4 *>(xyz + r0 * 3);
@@ -526,12 +530,12 @@ unsigned blocks_for(int64_t n_threads) { return (unsigned)((n_threads + kThreads
 
 }  // namespace
 
-cudaError_t launch_visibility(const float *xyz, int32_t n, const float cam[16], uint8_t *mask, int32_t *list,
+cudaError_t launch_visibility(const float *xyz, int32_t n, const float cam[kCamFloats], uint8_t *mask, int32_t *list,
                               unsigned long long *count, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    gs_camera c;
-    memcpy(&c, cam, sizeof(c));
+    CamArg c;
+    memcpy(c.c, cam, sizeof(c.c));
     if (((uintptr_t)xyz & 15u) == 0 && ((uintptr_t)mask & 3u) == 0)
         visibility4_kernel<<<blocks_for(((int64_t)n + kVisRpt - 1) / kVisRpt), kThreads, 0, s>>>(xyz, n, c, mask,
                                                                                                   list, count);

@@ -55,6 +55,10 @@ __host__ __device__ inline int slot_of_col(int c)
 
 enum VisSource : int { kVisAll = 0, kVisMask = 1, kVisCamera = 2 };
 
+// Floats of the camera argument the kernels take: gs_camera's 16, then the
+// frustum band constants (see frustum_visible).
+constexpr int kCamFloats = 20;
+
 // ------------------------------------------------------------ arguments
 
 struct StepArgs {
@@ -68,7 +72,7 @@ struct StepArgs {
     uint8_t *mask_out;           // optional
     unsigned long long *n_visible;  // optional, accumulated with atomicAdd
     int32_t *err;                // device error word (first error wins)
-    float cam[16];               // gs_camera as 16 floats
+    float cam[kCamFloats];       // gs_camera as 16 floats + the frustum band constants (camera_arg)
     float lr[6];
     float c1, c2;                // 1 - beta1, 1 - beta2 (FP32 of the FP64 values)
     float eps;
@@ -101,18 +105,43 @@ struct StepArgs {
 //
 // Fast path: FP32 with each product rounded and the sums taken left to right.
 // By the inner-product error bound (Higham, Accuracy and Stability of
-// Numerical Algorithms, Sec. 3.1) each computed coordinate is within
-// gamma_4 * S of the exact one, S = sum_j |R_rj mu_j| + |t_r|, and the side
-// test's product p_z tan rounds once more.  Wherever the FP32 slack to every
-// plane exceeds twice that error bound (2^-21 S >= 2 gamma_4 S; 2^-22 of
-// p_z tan for the extra rounding), the FP32 decision is the exact one.  A
-// mean inside the band (a few in a million for scenes of this extent) is
-// decided again in FP64: the products of FP32 values are exact there and the
-// sums round at 2^-53, so the decision is exact up to ~1e-14 of a plane.
+// Numerical Algorithms, Sec. 3.1) each computed coordinate p_r is within
+// gamma_4 S_r of the exact one, S_r = sum_j |R_rj mu_j| + |t_r| (gamma_4 =
+// 4u / (1 - 4u), u = 2^-24), and the side test's product p_z tan rounds once
+// more (within u of it).  The kernels take e = 2^-21 (rs max_j |mu_j| +
+// max_r |t_r|), rs = max_r sum_j |R_rj|, which bounds 2^-21 S_r for every r:
+// just under twice gamma_4 S_r.  Wherever each plane's FP32 slack exceeds
+// e for the near and far planes, and e (1 + tan) + 2^-22 p_z tan for the
+// sides, the FP32 decision is the exact one.  A mean inside that band (a
+// few per million for scenes of this extent) is decided again in FP64: the
+// products of FP32 values are exact there and the sums round at 2^-53, so the
+// decision is exact up to ~1e-14 of a plane.
+//
+// The camera as the kernels see it: the 16 floats of gs_camera, then
+// {2^-21 rs, 2^-21 max_r |t_r|, 1 + tan_x, 1 + tan_y} (camera_arg), each
+// rounded up.
+inline void camera_arg(const float *cam16, float *out)
+{
+    double rs = 0.0, tm = 0.0;
+    for (int r = 0; r < 3; ++r) {
+        double s = 0.0;
+        for (int j = 0; j < 3; ++j) s += cam16[3 * r + j] < 0 ? -(double)cam16[3 * r + j] : (double)cam16[3 * r + j];
+        rs = s > rs ? s : rs;
+        const double t = cam16[9 + r] < 0 ? -(double)cam16[9 + r] : (double)cam16[9 + r];
+        tm = t > tm ? t : tm;
+    }
+    constexpr double kUp = 1.0 + 0x1p-20;    // covers the rounding of these factors to FP32
+    for (int i = 0; i < 16; ++i) out[i] = cam16[i];
+    out[16] = (float)(rs * 0x1p-21 * kUp);
+    out[17] = (float)(tm * 0x1p-21 * kUp);
+    out[18] = (float)((1.0 + (double)cam16[12]) * kUp);
+    out[19] = (float)((1.0 + (double)cam16[13]) * kUp);
+}
+
 static __device__ __noinline__ bool frustum_visible_f64(float x, float y, float z, float c0, float c1, float c2,
-                                                 float c3, float c4, float c5, float c6, float c7, float c8,
-                                                 float t0, float t1, float t2, float tx, float ty, float zn,
-                                                 float zf)
+                                                        float c3, float c4, float c5, float c6, float c7, float c8,
+                                                        float t0, float t1, float t2, float tx, float ty, float zn,
+                                                        float zf)
 {
     const double X = x, Y = y, Z = z;
     const double px = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(c0, X), __dmul_rn(c1, Y)), __dmul_rn(c2, Z)), t0);
@@ -122,25 +151,20 @@ static __device__ __noinline__ bool frustum_visible_f64(float x, float y, float 
            (fabs(py) <= __dmul_rn(pz, (double)ty));
 }
 
+// c: kCamFloats floats (camera_arg).
 __device__ __forceinline__ bool frustum_visible(float x, float y, float z, const float *c)
 {
-    const float ax = __fmul_rn(c[0], x), bx = __fmul_rn(c[1], y), cx = __fmul_rn(c[2], z);
-    const float ay = __fmul_rn(c[3], x), by = __fmul_rn(c[4], y), cy = __fmul_rn(c[5], z);
-    const float az = __fmul_rn(c[6], x), bz = __fmul_rn(c[7], y), cz = __fmul_rn(c[8], z);
-    const float px = __fadd_rn(__fadd_rn(__fadd_rn(ax, bx), cx), c[9]);
-    const float py = __fadd_rn(__fadd_rn(__fadd_rn(ay, by), cy), c[10]);
-    const float pz = __fadd_rn(__fadd_rn(__fadd_rn(az, bz), cz), c[11]);
+    const float px = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[0], x), __fmul_rn(c[1], y)), __fmul_rn(c[2], z)), c[9]);
+    const float py = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[3], x), __fmul_rn(c[4], y)), __fmul_rn(c[5], z)), c[10]);
+    const float pz = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[6], x), __fmul_rn(c[7], y)), __fmul_rn(c[8], z)), c[11]);
     const float wx = __fmul_rn(pz, c[12]);
     const float wy = __fmul_rn(pz, c[13]);
     const bool vis = (pz >= c[14]) && (pz <= c[15]) && (fabsf(px) <= wx) && (fabsf(py) <= wy);
-    // twice the bound on the FP32 evaluation's error, per plane
-    constexpr float k2g4 = 0x1p-21f, k2u = 0x1p-22f;
-    const float ex = k2g4 * (fabsf(ax) + fabsf(bx) + fabsf(cx) + fabsf(c[9]));
-    const float ey = k2g4 * (fabsf(ay) + fabsf(by) + fabsf(cy) + fabsf(c[10]));
-    const float ez = k2g4 * (fabsf(az) + fabsf(bz) + fabsf(cz) + fabsf(c[11]));
-    const bool near_plane = (fabsf(pz - c[14]) <= ez) || (fabsf(c[15] - pz) <= ez) ||
-                            (fabsf(wx - fabsf(px)) <= ex + c[12] * ez + k2u * fabsf(wx)) ||
-                            (fabsf(wy - fabsf(py)) <= ey + c[13] * ez + k2u * fabsf(wy));
+    constexpr float k2u = 0x1p-22f;
+    const float e = fmaf(c[16], fmaxf(fmaxf(fabsf(x), fabsf(y)), fabsf(z)), c[17]);
+    const bool near_plane = (fabsf(pz - c[14]) <= e) || (fabsf(c[15] - pz) <= e) ||
+                            (fabsf(wx - fabsf(px)) <= fmaf(e, c[18], k2u * fabsf(wx))) ||
+                            (fabsf(wy - fabsf(py)) <= fmaf(e, c[19], k2u * fabsf(wy)));
     if (!near_plane) return vis;
     return frustum_visible_f64(x, y, z, c[0], c[1], c[2], c[3], c[4], c[5], c[6], c[7], c[8], c[9], c[10], c[11],
                                c[12], c[13], c[14], c[15]);
@@ -280,7 +304,7 @@ cudaError_t launch_batch(const BatchParams *p, unsigned *work, unsigned *done, i
 cudaError_t launch_active_rows(const float *tau, int32_t n, float tau_act, int32_t *blk, int32_t *rows,
                                long long *n_active, cudaStream_t s);
 int64_t active_rows_scratch(int64_t n);     // int32 entries of scratch launch_active_rows needs
-cudaError_t launch_visibility(const float *xyz, int32_t n, const float cam[16], uint8_t *mask,
+cudaError_t launch_visibility(const float *xyz, int32_t n, const float cam[kCamFloats], uint8_t *mask,
                               int32_t *list, unsigned long long *count, cudaStream_t s);
 cudaError_t launch_bias_table(double beta1, double beta2, int32_t len, double *t1, double *t2,
                               float2 *fac, cudaStream_t s);

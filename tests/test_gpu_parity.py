@@ -73,7 +73,19 @@ def _near_plane_means(cam, n, seed):
     sgn = np.where(side % 2 == 0, 1.0, -1.0)
     px = np.where(side < 2, sgn * pz * tx * (1 + d), rng.uniform(-1, 1, n) * pz * tx)
     py = np.where(side >= 2, sgn * pz * ty * (1 + d), rng.uniform(-1, 1, n) * pz * ty)
-    return ((np.stack([px, py, pz], 1) - t) @ R).astype(np.float32)
+    return np.linalg.solve(R, (np.stack([px, py, pz], 1) - t).T).T.astype(np.float32)
+
+
+def _skewed_camera():
+    """A camera whose R is not a rotation (scaled and sheared rows, a large
+    translation): the kernels' rounding band must hold for any 3x3 R."""
+    cam = synth.ring_cameras(4, (20.0,))[1].copy()
+    R = cam[:9].reshape(3, 3).astype(np.float64)
+    S = np.array([[2.5, 0.3, 0.0], [0.0, 0.7, -0.2], [0.1, 0.0, 1.6]])
+    cam[:9] = (S @ R).reshape(-1).astype(np.float32)
+    cam[9:12] = np.array([3.0, -7.5, 42.0], np.float32)
+    cam[12], cam[13] = np.float32(0.9), np.float32(0.4)
+    return cam
 
 
 def test_visibility_exact_near_planes(G, orc):
@@ -85,7 +97,7 @@ def test_visibility_exact_near_planes(G, orc):
     plane."""
     n = 200_003
     tot = {"near_plane": 0, "differ": 0, "differ_beyond_1e-9": 0, "fp32_differ_beyond_1e-6": 0}
-    for i, cam in enumerate(synth.ring_cameras(4, (-30.0, 0.0, 30.0))):
+    for i, cam in enumerate(synth.ring_cameras(4, (-30.0, 0.0, 30.0)) + [_skewed_camera()]):
         xyz_np = _near_plane_means(cam, n, 1200 + i)
         run = GpuScene({"xyz": xyz_np, "scale": np.zeros((n, 3), np.float32), "rot": np.zeros((n, 4), np.float32),
                         "opacity": np.zeros((n, 1), np.float32), "sh": np.zeros((n, 48), np.float32)})
