@@ -456,9 +456,11 @@ def run_ours(args):
         legs = {}
         for prec in ("fp32", "fp16_block", "bf16_hybrid", "bf16", "fp8_e4m3"):
             rr = timed_run(G, msc, prec, args.mixed_steps, 10)
+            tb, ta, _ = captured_traffic(mwl.name, prec)
             legs[prec] = {"value": rr["nv"] / rr["elapsed"], "hbm_gbs": rr["bytes_per_launch"] / rr["kern"] / 1e9,
                           "ms_per_step": rr["elapsed"] / args.mixed_steps * 1e3,
-                          "bytes_per_launch": rr["bytes_per_launch"]}
+                          "bytes_per_launch": rr["bytes_per_launch"],
+                          "traffic_over_algorithmic": tb / ta if tb else None}
             if args.mixed_error and prec != "fp32":
                 legs[prec]["error"] = error_vs_fp32(G, msc, prec)
         for prec in ("fp16_block", "bf16_hybrid", "bf16", "fp8_e4m3"):
