@@ -103,16 +103,16 @@ struct StepArgs {
 // Frustum test of one mean (z_near <= p_z <= z_far, |p_x| <= p_z tan_x,
 // |p_y| <= p_z tan_y with p = R mu + t), decided exactly.
 //
-// Fast path: FP32 with each product rounded and the sums taken left to right.
-// By the inner-product error bound (Higham, Accuracy and Stability of
-// Numerical Algorithms, Sec. 3.1) each computed coordinate p_r is within
-// gamma_4 S_r of the exact one, S_r = sum_j |R_rj mu_j| + |t_r| (gamma_4 =
-// 4u / (1 - 4u), u = 2^-24), and the side test's product p_z tan rounds once
-// more (within u of it).  The kernels take e = 2^-21 (rs max_j |mu_j| +
-// max_r |t_r|), rs = max_r sum_j |R_rj|, which bounds 2^-21 S_r for every r:
-// just under twice gamma_4 S_r.  Wherever each plane's FP32 slack exceeds
-// e for the near and far planes, and e (1 + tan) + 2^-22 p_z tan for the
-// sides, the FP32 decision is the exact one.  A mean inside that band (a
+// Fast path: FP32, each coordinate by three fused multiply-adds
+// (t_r + R_r2 mu_2, then + R_r1 mu_1, then + R_r0 mu_0) and each plane's slack
+// (p_z - z_near, z_far - p_z, p_z tan - |p_x|, p_z tan - |p_y|) by one more
+// rounding.  Unrolling the roundings, each computed coordinate is within
+// gamma_3 S_r of the exact one, S_r = sum_j |R_rj mu_j| + |t_r| (gamma_n =
+// n u / (1 - n u), u = 2^-24).  The kernels take e = 2^-21 (rs max_j |mu_j| +
+// max_r |t_r|), rs = max_r sum_j |R_rj|, which bounds 2^-21 S_r for every r,
+// more than twice gamma_3 S_r.  Wherever the slack exceeds e for the near and
+// far planes and e (1 + tan) for the sides, the FP32 decision is the exact
+// one (a slack's own rounding keeps its sign).  A mean inside that band (a
 // few per million for scenes of this extent) is decided again in FP64: the
 // products of FP32 values are exact there and the sums round at 2^-53, so the
 // decision is exact up to ~1e-14 of a plane.
@@ -154,17 +154,15 @@ static __device__ __noinline__ bool frustum_visible_f64(float x, float y, float 
 // c: kCamFloats floats (camera_arg).
 __device__ __forceinline__ bool frustum_visible(float x, float y, float z, const float *c)
 {
-    const float px = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[0], x), __fmul_rn(c[1], y)), __fmul_rn(c[2], z)), c[9]);
-    const float py = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[3], x), __fmul_rn(c[4], y)), __fmul_rn(c[5], z)), c[10]);
-    const float pz = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[6], x), __fmul_rn(c[7], y)), __fmul_rn(c[8], z)), c[11]);
-    const float wx = __fmul_rn(pz, c[12]);
-    const float wy = __fmul_rn(pz, c[13]);
-    const bool vis = (pz >= c[14]) && (pz <= c[15]) && (fabsf(px) <= wx) && (fabsf(py) <= wy);
-    constexpr float k2u = 0x1p-22f;
+    const float px = fmaf(c[0], x, fmaf(c[1], y, fmaf(c[2], z, c[9])));
+    const float py = fmaf(c[3], x, fmaf(c[4], y, fmaf(c[5], z, c[10])));
+    const float pz = fmaf(c[6], x, fmaf(c[7], y, fmaf(c[8], z, c[11])));
+    const float s_near = pz - c[14], s_far = c[15] - pz;
+    const float s_x = fmaf(pz, c[12], -fabsf(px)), s_y = fmaf(pz, c[13], -fabsf(py));
+    const bool vis = (s_near >= 0.f) && (s_far >= 0.f) && (s_x >= 0.f) && (s_y >= 0.f);
     const float e = fmaf(c[16], fmaxf(fmaxf(fabsf(x), fabsf(y)), fabsf(z)), c[17]);
-    const bool near_plane = (fabsf(pz - c[14]) <= e) || (fabsf(c[15] - pz) <= e) ||
-                            (fabsf(wx - fabsf(px)) <= fmaf(e, c[18], k2u * fabsf(wx))) ||
-                            (fabsf(wy - fabsf(py)) <= fmaf(e, c[19], k2u * fabsf(wy)));
+    const bool near_plane = (fabsf(s_near) <= e) || (fabsf(s_far) <= e) || (fabsf(s_x) <= e * c[18]) ||
+                            (fabsf(s_y) <= e * c[19]);
     if (!near_plane) return vis;
     return frustum_visible_f64(x, y, z, c[0], c[1], c[2], c[3], c[4], c[5], c[6], c[7], c[8], c[9], c[10], c[11],
                                c[12], c[13], c[14], c[15]);
