@@ -208,6 +208,18 @@ def test_active_rows_matches_oracle(G, orc, n):
         G.gs_active_rows(h, t_dev, None, cnt2)               # count only
         torch.cuda.synchronize()
         assert int(cnt2.item()) == want.size
+        # repeated calls on one context (each call a new epoch of the scan's
+        # status words), with different data in between
+        for rep in range(3):
+            tau2 = rng.normal(-5.5 + rep, 1.5, n).astype(np.float32)
+            t2 = torch.from_numpy(tau2).cuda()
+            rows.fill_(-1)
+            G.gs_active_rows(h, t2, rows, cnt)
+            torch.cuda.synchronize()
+            want2 = orc.active_rows(tau2)
+            assert int(cnt.item()) == want2.size
+            assert np.array_equal(rows.cpu().numpy()[:want2.size], want2)
+        assert G.gs_opt_sync_errors(h) == G.GS_OK
     G.gs_opt_destroy(h)
 
 
