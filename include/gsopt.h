@@ -448,13 +448,10 @@ gs_status gs_opt_import_state(gs_opt *opt, const float *m, const float *v, const
  *   opacity  device [n_rows] float32 logits tau, read-only.
  *   rows     device [n_rows] int32 out, optional (NULL: count only).
  *   n_active device int64 out (overwritten), required.
- * One launch: blocks of 4096 rows take their place in the list by a
- * decoupled look-back scan over the counts their predecessors publish.  A
- * scratch array of 8 B per 4096 rows (plus 16 B) is kept by the context
- * (allocated synchronously on first use or growth); calls on one context
- * must not overlap on the GPU.  Every device-side wait is bounded: if one
- * gives up, GS_ERR_TIMEOUT is recorded for gs_opt_sync_errors and the list
- * is not valid.
+ * Two launches (per-block counts; the ordered write, where each block adds
+ * up the counts of the blocks before it); a scratch array of one int32 per
+ * 4096 rows is kept by the context (allocated synchronously on first use or
+ * growth).
  */
 gs_status gs_active_rows(gs_opt *opt, const float *opacity, int32_t *rows, int64_t *n_active, void *stream);
 

@@ -36,7 +36,6 @@ struct gs_opt {
     unsigned long long *count_host = nullptr;  // pinned
     int32_t *act_blk = nullptr;   // gs_active_rows scratch, act_blk_len entries
     int64_t act_blk_len = 0;
-    uint32_t act_epoch = 0;       // gs_active_rows call number (status words carry it)
     double n_i = 0.0;
     bool latched = false;
     // cache of validated device allocation ranges [base, end)
@@ -649,9 +648,7 @@ gs_status gs_active_rows(gs_opt *o, const float *opacity, int32_t *rows, int64_t
     if (!n_active || !dev_ok(o, n_active, 8, 8) || !dev_ok(o, opacity, 4 * (size_t)n, 4) ||
         !dev_ok(o, rows, rows ? 4 * (size_t)n : 0, 4) || (n && !opacity))
         return GS_ERR_INVALID_ARG;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t need = gs::active_rows_scratch(n);
-    bool clear = false;
     if (need > o->act_blk_len) {
         cudaError_t e = cudaFree(o->act_blk);
         o->act_blk = nullptr;
@@ -659,18 +656,10 @@ gs_status gs_active_rows(gs_opt *o, const float *opacity, int32_t *rows, int64_t
         if (e == cudaSuccess) e = cudaMalloc(&o->act_blk, (size_t)need * sizeof(int32_t));
         if (e != cudaSuccess) return fail_cuda(o, e);
         o->act_blk_len = need;
-        clear = true;
     }
-    if (++o->act_epoch >= (1u << 30)) {       // after 2^30 calls: start the epochs again on a clean array
-        o->act_epoch = 1;
-        clear = true;
-    }
-    if (clear) {
-        cudaError_t e = cudaMemsetAsync(o->act_blk, 0, (size_t)o->act_blk_len * sizeof(int32_t), s);
-        if (e != cudaSuccess) return fail_cuda(o, e);
-    }
-    return fail_cuda(o, gs::launch_active_rows(opacity, (int32_t)n, active_threshold(), o->act_blk, o->act_epoch,
-                                               rows, reinterpret_cast<long long *>(n_active), o->err, s));
+    return fail_cuda(o, gs::launch_active_rows(opacity, (int32_t)n, active_threshold(), o->act_blk, rows,
+                                               reinterpret_cast<long long *>(n_active),
+                                               static_cast<cudaStream_t>(stream)));
 }
 
 gs_status gs_opt_export_state(gs_opt *o, float *m, float *v, uint32_t *t, void *stream)

@@ -442,68 +442,70 @@ __global__ void __launch_bounds__(kThreads) copy_rows_kernel(const CopyRowsArgs 
 }
 
 // ------------------------------------------------------------ active rows
-// The ascending list of rows with tau > tau_act (opacity > 1/255) in one pass
-// over blocks of kActRows rows, placed by a decoupled look-back scan (Merrill
-// & Garland, "Single-pass Parallel Prefix Scan with Decoupled Look-back",
-// 2016).  Blocks take their position from a ticket counter, so a block only
-// ever waits for blocks that started before it.  Each block counts its active
-// rows, publishes the count, looks back over its predecessors' published
-// counts (32 at a time, one warp) until it reaches an inclusive prefix,
-// publishes its own inclusive prefix and writes its rows.  Rows of a block are
-// taken as kActRpt strided passes of the CTA (coalesced loads, all in flight at
-// once), which is also their ascending order.
-//
-// Status word of a block: bits 62-63 the kind (1 count, 2 inclusive prefix),
-// bits 32-61 the call's epoch (words of earlier calls are ignored, so the
-// array needs no reset), bits 0-31 the value.  Every wait is bounded: after
-// kActMaxSpin polls the block records GS_ERR_TIMEOUT and publishes what it
-// has, so no block waits forever.
+// The ascending list of rows with tau > tau_act (opacity > 1/255) in two
+// passes over blocks of kActRows rows: per-block counts, then the ordered
+// write.  In the second pass every block adds up the counts of the blocks
+// before it (a few thousand ints, read from L2) to find its offset, so no
+// separate scan is needed; the last block also writes the total.  Rows of a
+// block are taken as kActRpt strided passes of the CTA (coalesced loads, all
+// in flight at once), which is also their ascending order.
 constexpr int kActRpt = 16;
 constexpr int kActRows = kThreads * kActRpt;
 constexpr int kActWarps = kThreads / 32;
-constexpr uint64_t kActCount = 1ull << 62, kActIncl = 2ull << 62;
-constexpr int kActMaxSpin = 1 << 20;
 
-__device__ __forceinline__ void st_release(unsigned long long *p, unsigned long long v)
+__global__ void __launch_bounds__(kThreads) active_count_kernel(const float *__restrict__ tau, int32_t n,
+                                                                float tau_act, int32_t *__restrict__ blk)
 {
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p)
-{
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
+    __shared__ int32_t warp_sum[kActWarps];
+    const int64_t r0 = (int64_t)blockIdx.x * kActRows;
+    float x[kActRpt];
+#pragma unroll
+    for (int j = 0; j < kActRpt; ++j) {
+        const int64_t r = r0 + j * kThreads + threadIdx.x;
+        x[j] = r < n ? __ldg(tau + r) : -INFINITY;      // kept in L2 for the write pass
+    }
+    int c = 0;
+#pragma unroll
+    for (int j = 0; j < kActRpt; ++j) c += x[j] > tau_act ? 1 : 0;
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int s = 0;
+        for (int w = 0; w < kActWarps; ++w) s += warp_sum[w];
+        blk[blockIdx.x] = s;
+    }
 }
 
-// scratch: [0] ticket counter, [1] finished-block counter, then the status
-// words (8-B aligned); rows == NULL: count only.
-__global__ void __launch_bounds__(kThreads) active_rows_kernel(const float *__restrict__ tau, int32_t n,
-                                                               float tau_act, unsigned *__restrict__ ctr,
-                                                               unsigned long long *__restrict__ status,
-                                                               uint32_t epoch, int32_t *__restrict__ rows,
-                                                               long long *__restrict__ total, int32_t *err)
+// rows == NULL: count only (only the last block runs, to write the total).
+__global__ void __launch_bounds__(kThreads) active_write_kernel(const float *__restrict__ tau, int32_t n,
+                                                                float tau_act, const int32_t *__restrict__ blk,
+                                                                int32_t *__restrict__ rows, long long *total)
 {
     __shared__ int32_t cnt[kActRpt * kActWarps];      // per (pass, warp), then its exclusive offset
-    __shared__ int s_blk;
+    __shared__ int32_t part[kActWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_blk = (int)atomicAdd(&ctr[0], 1u);
-    __syncthreads();
-    const int blk = s_blk;
-    const int64_t r0 = (int64_t)blk * kActRows;
+    const bool last = blockIdx.x == gridDim.x - 1;
+    if (!rows && !last) return;
+    const int64_t r0 = (int64_t)blockIdx.x * kActRows;
     float x[kActRpt];
 #pragma unroll
     for (int j = 0; j < kActRpt; ++j) {
         const int64_t r = r0 + j * kThreads + threadIdx.x;
         x[j] = r < n ? __ldcs(tau + r) : -INFINITY;
     }
+    int before = 0;                                      // counts of the blocks before this one
+    for (int b = threadIdx.x; b < (int)blockIdx.x; b += kThreads) before += blk[b];
+    before = __reduce_add_sync(0xffffffffu, before);
     unsigned bal[kActRpt];
 #pragma unroll
     for (int j = 0; j < kActRpt; ++j) {
         bal[j] = __ballot_sync(0xffffffffu, x[j] > tau_act);
         if (lane == 0) cnt[j * kActWarps + warp] = __popc(bal[j]);
     }
+    if (lane == 0) part[warp] = before;
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 0) {                                     // exclusive scan of the kActRpt*kActWarps counts
         constexpr int kPer = kActRpt * kActWarps / 32;
         int v[kPer], sum = 0;
 #pragma unroll
@@ -511,59 +513,29 @@ __global__ void __launch_bounds__(kThreads) active_rows_kernel(const float *__re
             v[q] = cnt[lane * kPer + q];
             sum += v[q];
         }
-        int incl = sum;                                  // inclusive scan over the lanes
+        int incl = sum;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, incl, d);
             if (lane >= d) incl += y;
         }
-        const uint32_t agg = (uint32_t)__shfl_sync(0xffffffffu, incl, 31);
-        const unsigned long long ep = (unsigned long long)epoch << 32;
-        if (lane == 0) st_release(&status[blk], (blk == 0 ? kActIncl : kActCount) | ep | agg);
-        uint32_t before = 0;
-        bool timed_out = false;
-        for (int p = blk - 1, spins = 0; p >= 0;) {
-            const int q = p - lane;
-            const unsigned long long w = q >= 0 ? ld_acquire(&status[q]) : (kActIncl | ep);
-            const bool valid = (w & (0x3fffffffull << 32)) == ep && (w >> 62) != 0;
-            const unsigned incl_mask = __ballot_sync(0xffffffffu, valid && (w >> 62) == 2);
-            const unsigned invalid = __ballot_sync(0xffffffffu, !valid);
-            const int first = incl_mask ? __ffs(incl_mask) - 1 : 31;   // nearest inclusive prefix
-            const unsigned need = first == 31 ? 0xffffffffu : (2u << first) - 1u;
-            if (invalid & need) {
-                if (++spins > kActMaxSpin) {
-                    timed_out = true;
-                    break;
-                }
-                __nanosleep(64);
-                continue;
-            }
-            before += __reduce_add_sync(0xffffffffu, lane <= first ? (uint32_t)w : 0u);
-            if (incl_mask) break;
-            p -= 32;
-        }
-        if (timed_out && lane == 0 && err) atomicCAS(err, 0, (int32_t)GS_ERR_TIMEOUT);
-        if (lane == 0 && blk != 0) st_release(&status[blk], kActIncl | ep | (before + agg));
-        int run = (int)before + incl - sum;
+        int base = 0;
+        for (int w = 0; w < kActWarps; ++w) base += part[w];
+        int run = base + incl - sum;
 #pragma unroll
         for (int q = 0; q < kPer; ++q) {
             cnt[lane * kPer + q] = run;
             run += v[q];
         }
-        if (blk == (int)gridDim.x - 1 && lane == 31 && total) *total = run;
+        if (last && lane == 31 && total) *total = run;
     }
     __syncthreads();
-    if (rows) {
-        const unsigned lt = (1u << lane) - 1u;
+    if (!rows) return;
+    const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
-        for (int j = 0; j < kActRpt; ++j)
-            if (bal[j] & (1u << lane))
-                rows[cnt[j * kActWarps + warp] + __popc(bal[j] & lt)] = (int32_t)(r0 + j * kThreads + threadIdx.x);
-    }
-    if (threadIdx.x == 0 && atomicAdd(&ctr[1], 1u) == gridDim.x - 1) {   // the last block resets the counters
-        ctr[0] = 0u;
-        ctr[1] = 0u;
-    }
+    for (int j = 0; j < kActRpt; ++j)
+        if (bal[j] & (1u << lane))
+            rows[cnt[j * kActWarps + warp] + __popc(bal[j] & lt)] = (int32_t)(r0 + j * kThreads + threadIdx.x);
 }
 
 unsigned blocks_for(int64_t n_threads) { return (unsigned)((n_threads + kThreads - 1) / kThreads); }
@@ -668,20 +640,15 @@ cudaError_t launch_copy_rows(const gs_attrs &a, const gs_grads &g, void *m, void
     return cudaGetLastError();
 }
 
-int64_t active_rows_scratch(int64_t n)
-{
-    // two counters and padding (16 B), then one 8-B status word per block
-    return 4 + 2 * std::max<int64_t>(1, (n + kActRows - 1) / kActRows);
-}
+int64_t active_rows_scratch(int64_t n) { return std::max<int64_t>(1, (n + kActRows - 1) / kActRows); }
 
-cudaError_t launch_active_rows(const float *tau, int32_t n, float tau_act, int32_t *scratch, uint32_t epoch,
-                               int32_t *rows, long long *n_active, int32_t *err, cudaStream_t s)
+cudaError_t launch_active_rows(const float *tau, int32_t n, float tau_act, int32_t *blk, int32_t *rows,
+                               long long *n_active, cudaStream_t s)
 {
     if (n <= 0) return cudaMemsetAsync(n_active, 0, sizeof(long long), s);
     const int32_t nblk = (int32_t)((n + kActRows - 1) / kActRows);
-    active_rows_kernel<<<nblk, kThreads, 0, s>>>(tau, n, tau_act, reinterpret_cast<unsigned *>(scratch),
-                                                 reinterpret_cast<unsigned long long *>(scratch + 4), epoch, rows,
-                                                 n_active, err);
+    active_count_kernel<<<nblk, kThreads, 0, s>>>(tau, n, tau_act, blk);
+    active_write_kernel<<<nblk, kThreads, 0, s>>>(tau, n, tau_act, blk, rows, n_active);
     return cudaGetLastError();
 }
 

@@ -299,11 +299,8 @@ int batch_candidates(int prec);
 void batch_candidate_info(int prec, int cand, int *tile, int *width, int *min_blocks);
 cudaError_t launch_batch(const BatchParams *p, unsigned *work, unsigned *done, int prec, int cand, cudaStream_t s,
                          int *grid, void **fn);
-// The ascending list of active rows in one pass (decoupled look-back);
-// scratch: active_rows_scratch(n) int32 entries, zero at first use; epoch:
-// 1 .. 2^30 - 1, a new value on every call (words of other epochs are ignored).
-cudaError_t launch_active_rows(const float *tau, int32_t n, float tau_act, int32_t *scratch, uint32_t epoch,
-                               int32_t *rows, long long *n_active, int32_t *err, cudaStream_t s);
+cudaError_t launch_active_rows(const float *tau, int32_t n, float tau_act, int32_t *blk, int32_t *rows,
+                               long long *n_active, cudaStream_t s);
 int64_t active_rows_scratch(int64_t n);     // int32 entries of scratch launch_active_rows needs
 cudaError_t launch_visibility(const float *xyz, int32_t n, const float cam[kCamFloats], uint8_t *mask,
                               int32_t *list, unsigned long long *count, cudaStream_t s);
