@@ -465,6 +465,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) step_tile_x(const StepAr
     using S = State<kPrec>;
     constexpr int kNsh = 48 / kW;
     __shared__ TileListsX<kTile> L;
+    pdl_enter();
     prefetch_tile_ahead<kTile>(a, vis_src);
     prefetch_tile_ahead_x<kTile>(a);
     const int64_t r0 = (int64_t)blockIdx.x * kTile;
@@ -526,8 +527,7 @@ cudaError_t launch_ext_t(const StepArgs &a, int vis_src, cudaStream_t s)
     StepArgs b = a;
     b.tile_ahead = resident_ctas(reinterpret_cast<const void *>(k), s_res);
     const unsigned grid = (unsigned)((a.n_rows + kExtTile - 1) / kExtTile);
-    k<<<grid, kThreads, 0, s>>>(b, vis_src);
-    return cudaGetLastError();
+    return launch_pdl(k, grid, s, b, vis_src);
 }
 
 }  // namespace

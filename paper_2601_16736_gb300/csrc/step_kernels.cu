@@ -165,6 +165,7 @@ template <int kTile, int kMinBlocks, int kPrec, int kW>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) step_tile(const StepArgs a, const int vis_src)
 {
     __shared__ TileLists<kTile> L;
+    pdl_enter();
     prefetch_tile_ahead<kTile>(a, vis_src);
     process_tile<kTile, kPrec, kW>(a, vis_src, (int64_t)blockIdx.x * kTile, L);
 }
@@ -234,8 +235,7 @@ cudaError_t launch_tiles(const StepArgs &a, int vis_src, cudaStream_t s)
     StepArgs b = a;
     b.tile_ahead = resident_ctas(reinterpret_cast<const void *>(k), s_res);
     const unsigned n_tiles = (unsigned)((a.n_rows + kStepTile - 1) / kStepTile);
-    k<<<n_tiles, kThreads, 0, s>>>(b, vis_src);
-    return cudaGetLastError();
+    return launch_pdl(k, n_tiles, s, b, vis_src);
 }
 
 }  // namespace
