@@ -247,7 +247,8 @@ def timed_run(G, sc, prec, steps, warmup, clocks_device=None, dist=None, extra=N
             sampler.start()
             time.sleep(0.3)
         torch.cuda.synchronize()
-        torch.cuda.nvtx.range_push("timed")      # lets a profiler restrict its launch list to this region
+        if not per_launch:                     # lets a profiler restrict its launch list to the timed region
+            torch.cuda.nvtx.range_push("timed")
         t0.record(stream)
         for j in range(steps):
             if per_launch:
@@ -257,7 +258,8 @@ def timed_run(G, sc, prec, steps, warmup, clocks_device=None, dist=None, extra=N
                 ev[j][1].record(stream)
         t1.record(stream)
         torch.cuda.synchronize()
-        torch.cuda.nvtx.range_pop()
+        if not per_launch:
+            torch.cuda.nvtx.range_pop()
         if dist is not None:
             dist.barrier()
         clocks = sampler.stop() if sampler else None
