@@ -4,12 +4,18 @@ Headline (``value``): the 1 M-primitive workload — 59 FP32 attributes per
 primitive (xyz 3, log-scale 3, quaternion 4, opacity logit 1, SH degree 3 48),
 means in 64 Gaussian blobs, 200 ring/elevation views in random order (about
 30 % of the primitives visible per view), DAR on opacity and scale every step,
-RSR every 100 steps (StSS ratio 0.1), FP32 moments.  One step = one launch of
-the fused step kernel over all rows.
+RSR every 100 steps (StSS ratio 0.1, an RSR step inside every timed window),
+FP32 moments.  One step = one launch of the fused step kernel over all rows;
+the timed steps run back to back between two region events.
 
-``mixed_precision``: the 3 M-primitive workload (about 20 % visible) timed
-with FP32, BF16-hybrid and all-BF16 moments, each with its error against the
-FP64 oracle after 1000 steps on 2000 sampled primitives (group relative L2).
+Beside it in the same line: ``roofline`` (algorithmic bytes per step against
+the measured copy bandwidth; DRAM traffic from the committed ncu capture of
+this kernel build), ``e2e`` (the host-gradient call), per-launch percentiles
+from a second instrumented pass, the blob-sorted row order, the 100 k
+(L2-resident) workload, mixed-precision moments on the 1 M and 3 M workloads
+with their error against the FP32 step, the optional terms, the access
+ceiling, the re-index and batched workloads, the GPU's frustum decisions
+against the FP64 oracle, and the oracle itself on the host cores.
 
 Prints one JSON line.  Multi-GPU (torchrun): every rank runs an independent
 replica on its own scene (rows are independent; no data exchange); value =
