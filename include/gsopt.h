@@ -359,8 +359,9 @@ gs_status gs_batch_graph_step(gs_batch *b, const gs_attrs *attrs, const gs_grads
                               const gs_step_params *params, int64_t *n_visible, void *stream);
 
 /* The launch configuration in use: rows per tile, SH columns per work item,
- * CTAs per SM, and whether tuning has finished (1) or not (0).  Any output
- * may be NULL. */
+ * CTAs per SM of the persistent form (0: one CTA per tile of the whole batch,
+ * scheduled by the hardware), and whether tuning has finished (1) or not (0).
+ * Any output may be NULL. */
 gs_status gs_batch_config(const gs_batch *b, int32_t *tile_rows, int32_t *sh_width, int32_t *blocks_per_sm,
                           int32_t *tuned);
 

@@ -733,8 +733,9 @@ struct gs_batch {
     // graph
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    cudaGraphNode_t copy_node = nullptr;
+    cudaGraphNode_t copy_node = nullptr, kern_node = nullptr;
     size_t graph_bytes = 0;
+    int graph_grid = 0;
 };
 
 namespace {
@@ -836,32 +837,39 @@ gs_status batch_run(gs_batch *b, const gs_attrs *attrs, const gs_grads *grads, c
     if (e == cudaSuccess) e = batch_slot(b, &slot);
     if (e != cudaSuccess) return fail_cuda(o0, e);
     batch_fill(b, cand, attrs, grads, cams, params, n_visible, b->h_slot[slot]);
+    const int total_tiles = b->h_slot[slot]->total_tiles;
     const size_t bytes = batch_bytes((int)b->scenes.size());
     if (graph && b->best >= 0) {
+        int grid = 0;
+        void *fn = nullptr;
+        if ((e = gs::launch_batch(b->d_params, b->d_counters, b->d_counters + 1, total_tiles, b->prec, cand, s, &grid,
+                                  &fn)) != cudaSuccess)
+            return fail_cuda(o0, e);
+        cudaKernelNodeParams kp = {};
+        unsigned *work = b->d_counters, *done = b->d_counters + 1;
+        void *args[3] = {&b->d_params, &work, &done};
+        kp.func = fn;
+        kp.gridDim = dim3((unsigned)grid);
+        kp.blockDim = dim3(256);
+        kp.kernelParams = args;
         if (!b->exec) {
-            int grid = 0;
-            void *fn = nullptr;
-            if ((e = gs::launch_batch(b->d_params, b->d_counters, b->d_counters + 1, b->prec, cand, s, &grid, &fn)) !=
-                cudaSuccess)
-                return fail_cuda(o0, e);
-            cudaGraphNode_t kern = nullptr;
-            cudaKernelNodeParams kp = {};
-            unsigned *work = b->d_counters, *done = b->d_counters + 1;
-            void *args[3] = {&b->d_params, &work, &done};
-            kp.func = fn;
-            kp.gridDim = dim3((unsigned)grid);
-            kp.blockDim = dim3(256);
-            kp.kernelParams = args;
             if ((e = cudaGraphCreate(&b->graph, 0)) != cudaSuccess ||
                 (e = cudaGraphAddMemcpyNode1D(&b->copy_node, b->graph, nullptr, 0, b->d_params, b->h_slot[slot], bytes,
                                               cudaMemcpyHostToDevice)) != cudaSuccess ||
-                (e = cudaGraphAddKernelNode(&kern, b->graph, &b->copy_node, 1, &kp)) != cudaSuccess ||
+                (e = cudaGraphAddKernelNode(&b->kern_node, b->graph, &b->copy_node, 1, &kp)) != cudaSuccess ||
                 (e = cudaGraphInstantiate(&b->exec, b->graph, 0)) != cudaSuccess)
                 return fail_cuda(o0, e);
             b->graph_bytes = bytes;
-        } else if ((e = cudaGraphExecMemcpyNodeSetParams1D(b->exec, b->copy_node, b->d_params, b->h_slot[slot], bytes,
-                                                             cudaMemcpyHostToDevice)) != cudaSuccess) {
-            return fail_cuda(o0, e);
+            b->graph_grid = grid;
+        } else {
+            if ((e = cudaGraphExecMemcpyNodeSetParams1D(b->exec, b->copy_node, b->d_params, b->h_slot[slot], bytes,
+                                                        cudaMemcpyHostToDevice)) != cudaSuccess)
+                return fail_cuda(o0, e);
+            if (grid != b->graph_grid) {      // the one-CTA-per-tile form follows the scenes' sizes
+                if ((e = cudaGraphExecKernelNodeSetParams(b->exec, b->kern_node, &kp)) != cudaSuccess)
+                    return fail_cuda(o0, e);
+                b->graph_grid = grid;
+            }
         }
         e = cudaGraphLaunch(b->exec, s);
         if (e == cudaSuccess) e = cudaEventRecord(b->slot_ev[slot], s);
@@ -875,7 +883,8 @@ gs_status batch_run(gs_batch *b, const gs_attrs *attrs, const gs_grads *grads, c
     b->slot_pending[slot] = true;
     if (timed) e = cudaEventRecord(b->ev[2 * b->calls], s);
     if (e == cudaSuccess)
-        e = gs::launch_batch(b->d_params, b->d_counters, b->d_counters + 1, b->prec, cand, s, nullptr, nullptr);
+        e = gs::launch_batch(b->d_params, b->d_counters, b->d_counters + 1, total_tiles, b->prec, cand, s, nullptr,
+                             nullptr);
     if (e == cudaSuccess && timed) e = cudaEventRecord(b->ev[2 * b->calls + 1], s);
     if (e != cudaSuccess) return fail_cuda(o0, e);
     if (timed) ++b->calls;

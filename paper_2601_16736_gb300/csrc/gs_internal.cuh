@@ -293,12 +293,14 @@ cudaError_t launch_step(const StepArgs &a, int prec, int vis_src, cudaStream_t s
 cudaError_t launch_step_ext(const StepArgs &a, int prec, int vis_src, cudaStream_t s);
 // Batched launch with candidate configuration `cand` (0 .. batch_candidates-1)
 // over the device scene table p (tile_start built for that candidate's tile
-// size, see batch_candidate_info); *grid receives the persistent grid.  With
-// fn != NULL nothing is launched: *fn receives the kernel (for graph nodes).
+// size, see batch_candidate_info; total_tiles its tile count); *grid receives
+// the grid (the persistent grid, or total_tiles for the one-CTA-per-tile
+// form, min_blocks 0).  With fn != NULL nothing is launched: *fn receives the
+// kernel (for graph nodes).
 int batch_candidates(int prec);
 void batch_candidate_info(int prec, int cand, int *tile, int *width, int *min_blocks);
-cudaError_t launch_batch(const BatchParams *p, unsigned *work, unsigned *done, int prec, int cand, cudaStream_t s,
-                         int *grid, void **fn);
+cudaError_t launch_batch(const BatchParams *p, unsigned *work, unsigned *done, int total_tiles, int prec, int cand,
+                         cudaStream_t s, int *grid, void **fn);
 cudaError_t launch_active_rows(const float *tau, int32_t n, float tau_act, int32_t *blk, int32_t *rows,
                                long long *n_active, cudaStream_t s);
 int64_t active_rows_scratch(int64_t n);     // int32 entries of scratch launch_active_rows needs

@@ -214,6 +214,31 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) step_batch(const BatchPa
     }
 }
 
+// Many scenes in one launch with one CTA per tile of the whole batch: CTA t
+// finds its scene (the last whose first tile is <= t), copies that scene's
+// arguments into shared memory and runs the tile.  The hardware schedules
+// the CTAs as it does a single scene's; the tuner weighs this against the
+// persistent form.  work and done are unused (same signature).
+template <int kTile, int kMinBlocks, int kPrec, int kW>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) step_batch_grid(const BatchParams *__restrict__ p,
+                                                                         unsigned *, unsigned *)
+{
+    __shared__ TileLists<kTile> L;
+    __shared__ StepArgs sa;
+    const int t = (int)blockIdx.x;
+    if (t >= p->total_tiles) return;
+    int lo = 0, hi = p->n_scenes - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (p->tile_start[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(&p->args[lo]);
+    uint32_t *dst = reinterpret_cast<uint32_t *>(&sa);
+    for (int q = threadIdx.x; q < (int)(sizeof(StepArgs) / 4); q += kThreads) dst[q] = src[q];
+    __syncthreads();
+    process_tile<kTile, kPrec, kW>(sa, kVisCamera, (int64_t)(t - p->tile_start[lo]) * kTile, L);
+}
+
 }  // namespace
 
 constexpr int kStepTile = 256;
@@ -259,7 +284,22 @@ cudaError_t launch_step(const StepArgs &a, int prec, int vis_src, cudaStream_t s
 namespace {
 
 template <int kTile, int kMinBlocks, int kPrec, int kW>
-cudaError_t launch_batch_t(const BatchParams *p, unsigned *work, unsigned *done, cudaStream_t s, int *grid_out,
+cudaError_t launch_batch_grid_t(const BatchParams *p, unsigned *work, unsigned *done, int total_tiles, cudaStream_t s,
+                                int *grid_out, void **fn_out)
+{
+    auto k = step_batch_grid<kTile, kMinBlocks, kPrec, kW>;
+    const int grid = std::max(1, total_tiles);
+    if (grid_out) *grid_out = grid;
+    if (fn_out) {                              // only report the kernel and its grid
+        *fn_out = reinterpret_cast<void *>(k);
+        return cudaSuccess;
+    }
+    k<<<grid, kThreads, 0, s>>>(p, work, done);
+    return cudaGetLastError();
+}
+
+template <int kTile, int kMinBlocks, int kPrec, int kW>
+cudaError_t launch_batch_t(const BatchParams *p, unsigned *work, unsigned *done, int, cudaStream_t s, int *grid_out,
                            void **fn_out)
 {
     auto k = step_batch<kTile, kMinBlocks, kPrec, kW>;
@@ -283,8 +323,10 @@ cudaError_t launch_batch_t(const BatchParams *p, unsigned *work, unsigned *done,
     return cudaGetLastError();
 }
 
-using BatchFn = cudaError_t (*)(const BatchParams *, unsigned *, unsigned *, cudaStream_t, int *, void **);
+using BatchFn = cudaError_t (*)(const BatchParams *, unsigned *, unsigned *, int, cudaStream_t, int *, void **);
 
+// min_blocks 0 marks the one-CTA-per-tile form (5 CTAs per SM), otherwise the
+// persistent form with that many resident CTAs per SM.
 struct BatchCandidate {
     int tile, width, min_blocks;
     BatchFn fn;
@@ -294,6 +336,7 @@ const BatchCandidate kCandF32[] = {
     {256, 4, 4, launch_batch_t<256, 4, GS_MOM_FP32, 4>}, {512, 4, 4, launch_batch_t<512, 4, GS_MOM_FP32, 4>},
     {256, 4, 3, launch_batch_t<256, 3, GS_MOM_FP32, 4>}, {256, 8, 4, launch_batch_t<256, 4, GS_MOM_FP32, 8>},
     {256, 4, 5, launch_batch_t<256, 5, GS_MOM_FP32, 4>}, {512, 4, 5, launch_batch_t<512, 5, GS_MOM_FP32, 4>},
+    {256, 4, 0, launch_batch_grid_t<256, 5, GS_MOM_FP32, 4>},
 };
 const BatchCandidate kCandBf16[] = {
     {256, 8, 4, launch_batch_t<256, 4, GS_MOM_BF16, 8>}, {512, 8, 4, launch_batch_t<512, 4, GS_MOM_BF16, 8>},
@@ -309,15 +352,16 @@ const BatchCandidate kCandF16B[] = {
     {256, 8, 4, launch_batch_t<256, 4, GS_MOM_FP16_BLOCK, 8>},
     {512, 8, 4, launch_batch_t<512, 4, GS_MOM_FP16_BLOCK, 8>},
     {256, 8, 5, launch_batch_t<256, 5, GS_MOM_FP16_BLOCK, 8>},
+    {256, 8, 0, launch_batch_grid_t<256, 5, GS_MOM_FP16_BLOCK, 8>},
 };
 
 const BatchCandidate *candidates(int prec, int *n)
 {
     switch (prec) {
-    case GS_MOM_FP32: *n = 6; return kCandF32;
+    case GS_MOM_FP32: *n = 7; return kCandF32;
     case GS_MOM_BF16: *n = 3; return kCandBf16;
     case GS_MOM_BF16_HYBRID: *n = 3; return kCandHyb;
-    case GS_MOM_FP16_BLOCK: *n = 3; return kCandF16B;
+    case GS_MOM_FP16_BLOCK: *n = 4; return kCandF16B;
     default: *n = 0; return nullptr;
     }
 }
@@ -335,13 +379,13 @@ void batch_candidate_info(int prec, int c, int *tile, int *width, int *min_block
     *min_blocks = cs[c].min_blocks;
 }
 
-cudaError_t launch_batch(const BatchParams *p, unsigned *work, unsigned *done, int prec, int cand, cudaStream_t s,
-                         int *grid, void **fn)
+cudaError_t launch_batch(const BatchParams *p, unsigned *work, unsigned *done, int total_tiles, int prec, int cand,
+                         cudaStream_t s, int *grid, void **fn)
 {
     int n = 0;
     const BatchCandidate *cs = candidates(prec, &n);
     if (cand < 0 || cand >= n) return cudaErrorInvalidValue;
-    return cs[cand].fn(p, work, done, s, grid, fn);
+    return cs[cand].fn(p, work, done, total_tiles, s, grid, fn);
 }
 
 }  // namespace gs
