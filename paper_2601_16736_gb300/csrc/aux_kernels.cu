@@ -32,6 +32,7 @@ __global__ void __launch_bounds__(kThreads) visibility_kernel(const float *__res
 {
     __shared__ int32_t s_cnt[kThreads / 32];
     __shared__ unsigned long long s_base;
+    pdl_enter();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t row = (int64_t)blockIdx.x * kThreads + tid;
     const float *c = cam.c;
@@ -74,6 +75,7 @@ __global__ void __launch_bounds__(kThreads) visibility4_kernel(const float *__re
 {
     __shared__ int32_t s_warp[kThreads / 32];
     __shared__ unsigned long long s_base;
+    pdl_enter();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t r0 = ((int64_t)blockIdx.x * kThreads + tid) * kVisRpt;
     const float *c = cam.c;
@@ -395,6 +397,7 @@ __device__ __forceinline__ float4 xor4(float4 x, uint32_t b)
 
 __global__ void __launch_bounds__(kThreads) copy_rows_kernel(const CopyRowsArgs c)
 {
+    pdl_enter();
     const int64_t nl = c.nl, e_sh = 12 * nl, e_m = e_sh + (int64_t)c.chunks * nl, e_st = e_m + (int64_t)c.chunks * nl;
     const int64_t total = e_st + 4 * nl;
     for (int64_t w = (int64_t)blockIdx.x * kThreads + threadIdx.x; w < total; w += (int64_t)gridDim.x * kThreads) {
@@ -457,6 +460,7 @@ __global__ void __launch_bounds__(kThreads) active_count_kernel(const float *__r
                                                                 float tau_act, int32_t *__restrict__ blk)
 {
     __shared__ int32_t warp_sum[kActWarps];
+    pdl_enter();
     const int64_t r0 = (int64_t)blockIdx.x * kActRows;
     float x[kActRpt];
 #pragma unroll
@@ -484,6 +488,7 @@ __global__ void __launch_bounds__(kThreads) active_write_kernel(const float *__r
 {
     __shared__ int32_t cnt[kActRpt * kActWarps];      // per (pass, warp), then its exclusive offset
     __shared__ int32_t part[kActWarps];
+    pdl_enter();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool last = blockIdx.x == gridDim.x - 1;
     if (!rows && !last) return;
@@ -549,11 +554,9 @@ cudaError_t launch_visibility(const float *xyz, int32_t n, const float cam[kCamF
     CamArg c;
     memcpy(c.c, cam, sizeof(c.c));
     if (((uintptr_t)xyz & 15u) == 0 && ((uintptr_t)mask & 3u) == 0)
-        visibility4_kernel<<<blocks_for(((int64_t)n + kVisRpt - 1) / kVisRpt), kThreads, 0, s>>>(xyz, n, c, mask,
-                                                                                                  list, count);
-    else
-        visibility_kernel<<<blocks_for(n), kThreads, 0, s>>>(xyz, n, c, mask, list, count);
-    return cudaGetLastError();
+        return launch_pdl(visibility4_kernel, blocks_for(((int64_t)n + kVisRpt - 1) / kVisRpt), kThreads, s, xyz, n, c,
+                          mask, list, count);
+    return launch_pdl(visibility_kernel, blocks_for(n), kThreads, s, xyz, n, c, mask, list, count);
 }
 
 cudaError_t launch_bias_table(double beta1, double beta2, int32_t len, double *t1, double *t2, float2 *fac,
@@ -636,8 +639,7 @@ cudaError_t launch_copy_rows(const gs_attrs &a, const gs_grads &g, void *m, void
     if (e != cudaSuccess) return e;
     const int64_t items = (16 + 2 * (int64_t)c.chunks) * n_listed;
     const unsigned grid = (unsigned)std::min<int64_t>((items + kThreads - 1) / kThreads, 8 * (int64_t)sms);
-    copy_rows_kernel<<<grid, kThreads, 0, s>>>(c);
-    return cudaGetLastError();
+    return launch_pdl(copy_rows_kernel, grid, kThreads, s, c);
 }
 
 int64_t active_rows_scratch(int64_t n) { return std::max<int64_t>(1, (n + kActRows - 1) / kActRows); }
@@ -647,9 +649,10 @@ cudaError_t launch_active_rows(const float *tau, int32_t n, float tau_act, int32
 {
     if (n <= 0) return cudaMemsetAsync(n_active, 0, sizeof(long long), s);
     const int32_t nblk = (int32_t)((n + kActRows - 1) / kActRows);
-    active_count_kernel<<<nblk, kThreads, 0, s>>>(tau, n, tau_act, blk);
-    active_write_kernel<<<nblk, kThreads, 0, s>>>(tau, n, tau_act, blk, rows, n_active);
-    return cudaGetLastError();
+    cudaError_t e = launch_pdl(active_count_kernel, (unsigned)nblk, kThreads, s, tau, n, tau_act, blk);
+    if (e != cudaSuccess) return e;
+    return launch_pdl(active_write_kernel, (unsigned)nblk, kThreads, s, tau, n, tau_act,
+                      static_cast<const int32_t *>(blk), rows, n_active);
 }
 
 }  // namespace gs

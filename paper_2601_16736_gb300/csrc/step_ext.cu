@@ -527,7 +527,7 @@ cudaError_t launch_ext_t(const StepArgs &a, int vis_src, cudaStream_t s)
     StepArgs b = a;
     b.tile_ahead = resident_ctas(reinterpret_cast<const void *>(k), s_res);
     const unsigned grid = (unsigned)((a.n_rows + kExtTile - 1) / kExtTile);
-    return launch_pdl(k, grid, s, b, vis_src);
+    return launch_pdl(k, grid, kThreads, s, b, vis_src);
 }
 
 }  // namespace

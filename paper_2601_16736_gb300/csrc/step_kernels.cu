@@ -260,7 +260,7 @@ cudaError_t launch_tiles(const StepArgs &a, int vis_src, cudaStream_t s)
     StepArgs b = a;
     b.tile_ahead = resident_ctas(reinterpret_cast<const void *>(k), s_res);
     const unsigned n_tiles = (unsigned)((a.n_rows + kStepTile - 1) / kStepTile);
-    return launch_pdl(k, n_tiles, s, b, vis_src);
+    return launch_pdl(k, n_tiles, kThreads, s, b, vis_src);
 }
 
 }  // namespace
