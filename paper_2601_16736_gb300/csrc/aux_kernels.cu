@@ -320,52 +320,91 @@ __global__ void import_f16b_kernel(const StateView st, int32_t n, const float *_
 }
 
 // ----------------------------------------------------------- attribute gather
-// A flat index space: first one thread per float4 of the 16-B aligned groups
-// (12 SH float4 and the rotation of each row), then one thread per row for
-// its seven small values (xyz, scale, opacity).  Consecutive threads write
-// consecutive output addresses, and read consecutive input addresses wherever
-// the sources run in order (a prune keeps them so).  Nothing is read again,
-// so loads and stores stream past L2.
+// Two flat index spaces, each walked four items per thread (float4, or
+// float) with all loads issued before the stores, so a thread keeps four
+// accesses in flight (eight floats per thread measured slower):
+// first one item per float4 of the 16-B aligned groups (12 SH float4 and the
+// rotation of each row), then one item per float of the small groups (xyz,
+// scale, opacity).  Consecutive items write consecutive output addresses, and
+// read consecutive input addresses wherever the sources run in order (a prune
+// keeps them so).  Nothing is read again, so loads and stores stream past L2.
 constexpr int kGatherVec = 13;
+constexpr int kGatherU = 4, kGatherSmallU = 4;
 
-__global__ void gather_attrs_kernel(const gs_attrs in, int32_t n_in, const gs_attrs out,
-                                    const int32_t *__restrict__ src, int32_t n_new, int32_t *err)
+__global__ void __launch_bounds__(kThreads) gather_vec_kernel(const gs_attrs in, int32_t n_in, const gs_attrs out,
+                                                              const int32_t *__restrict__ src, int32_t n_new,
+                                                              int32_t *err)
 {
-    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t n = n_new;
-    if (gid < kGatherVec * n) {
-        const int64_t j = gid / kGatherVec;
-        const int k = (int)(gid - kGatherVec * j);
+    const int64_t total = (int64_t)kGatherVec * n_new;
+    const int64_t base = (int64_t)blockIdx.x * kThreads * kGatherU + threadIdx.x;
+    float4 v[kGatherU];
+    float4 *dst[kGatherU];
+#pragma unroll
+    for (int u = 0; u < kGatherU; ++u) {
+        const int64_t idx = base + (int64_t)u * kThreads;
+        dst[u] = nullptr;
+        if (idx >= total) continue;
+        const int64_t j = idx / kGatherVec;
+        const int k = (int)(idx - kGatherVec * j);
         const int32_t s = src[j];
-        if (s < 0) return;
+        if (s < 0) continue;
         if (s >= n_in) {
             if (k == 0) record_error(err, GS_ERR_INVALID_ARG);
-            return;
+            continue;
         }
-        if (k < 12)
-            __stcs(reinterpret_cast<float4 *>(out.sh) + j * 12 + k,
-                   __ldcs(reinterpret_cast<const float4 *>(in.sh) + (int64_t)s * 12 + k));
-        else
-            __stcs(reinterpret_cast<float4 *>(out.rot) + j, __ldcs(reinterpret_cast<const float4 *>(in.rot) + s));
-    } else if (gid < (kGatherVec + 1) * n) {
-        const int64_t j = gid - kGatherVec * n;
-        const int32_t s = src[j];
-        if (s < 0 || s >= n_in) return;            // an out-of-range source is recorded above
-        const int64_t r = s;
-        const float x0 = __ldcs(in.xyz + r * 3), x1 = __ldcs(in.xyz + r * 3 + 1), x2 = __ldcs(in.xyz + r * 3 + 2);
-        const float s0 = __ldcs(in.scale + r * 3), s1 = __ldcs(in.scale + r * 3 + 1), s2 = __ldcs(in.scale + r * 3 + 2);
-        const float op = __ldcs(in.opacity + r);
-        __stcs(out.xyz + j * 3, x0); __stcs(out.xyz + j * 3 + 1, x1); __stcs(out.xyz + j * 3 + 2, x2);
-        __stcs(out.scale + j * 3, s0); __stcs(out.scale + j * 3 + 1, s1); __stcs(out.scale + j * 3 + 2, s2);
-        __stcs(out.opacity + j, op);
+        if (k < 12) {
+            v[u] = __ldcs(reinterpret_cast<const float4 *>(in.sh) + (int64_t)s * 12 + k);
+            dst[u] = reinterpret_cast<float4 *>(out.sh) + j * 12 + k;
+        } else {
+            v[u] = __ldcs(reinterpret_cast<const float4 *>(in.rot) + s);
+            dst[u] = reinterpret_cast<float4 *>(out.rot) + j;
+        }
     }
+#pragma unroll
+    for (int u = 0; u < kGatherU; ++u)
+        if (dst[u]) __stcs(dst[u], v[u]);
+}
+
+// Items 0 .. 3n-1: xyz floats, 3n .. 6n-1: scale floats, 6n .. 7n-1: opacity.
+// An out-of-range source is recorded by gather_vec_kernel.
+__global__ void __launch_bounds__(kThreads) gather_small_kernel(const gs_attrs in, int32_t n_in, const gs_attrs out,
+                                                                const int32_t *__restrict__ src, int32_t n_new)
+{
+    const int64_t n = n_new, total = 7 * n;
+    const int64_t base = (int64_t)blockIdx.x * kThreads * kGatherSmallU + threadIdx.x;
+    float v[kGatherSmallU];
+    float *dst[kGatherSmallU];
+#pragma unroll
+    for (int u = 0; u < kGatherSmallU; ++u) {
+        const int64_t idx = base + (int64_t)u * kThreads;
+        dst[u] = nullptr;
+        if (idx >= total) continue;
+        const float *a;
+        float *o;
+        int64_t e, j;
+        int c;
+        if (idx < 3 * n) {
+            e = idx; j = e / 3; c = (int)(e - 3 * j); a = in.xyz; o = out.xyz;
+        } else if (idx < 6 * n) {
+            e = idx - 3 * n; j = e / 3; c = (int)(e - 3 * j); a = in.scale; o = out.scale;
+        } else {
+            e = idx - 6 * n; j = e; c = 0; a = in.opacity; o = out.opacity;
+        }
+        const int32_t s = src[j];
+        if (s < 0 || s >= n_in) continue;
+        const int w = idx < 6 * n ? 3 : 1;
+        v[u] = __ldcs(a + (int64_t)s * w + c);
+        dst[u] = o + e;
+    }
+#pragma unroll
+    for (int u = 0; u < kGatherSmallU; ++u)
+        if (dst[u]) __stcs(dst[u], v[u]);
 }
 
 // ------------------------------------------------------------- row copy
 // The memory traffic of a step over listed rows, without the update: each
 // byte a visible row's step reads is read, each byte it writes is written
-// back with the value read.  Gradient loads are volatile so they are issued
-// although their values are unused.  Items are kind-major (SH chunks, then
+// back with the value read.  Items are kind-major (SH chunks, then
 // moment-row chunks, then the four small groups) so warps stay convergent.
 struct CopyRowsArgs {
     gs_attrs a;
@@ -622,7 +661,12 @@ cudaError_t launch_gather_attrs(const gs_attrs &in, int32_t n_in, const gs_attrs
                                 int32_t n_new, int32_t *err, cudaStream_t s)
 {
     if (n_new <= 0) return cudaSuccess;
-    gather_attrs_kernel<<<blocks_for((int64_t)n_new * (kGatherVec + 1)), kThreads, 0, s>>>(in, n_in, out, src, n_new, err);
+    const int64_t per_cta = (int64_t)kThreads * kGatherU;
+    gather_vec_kernel<<<(unsigned)(((int64_t)kGatherVec * n_new + per_cta - 1) / per_cta), kThreads, 0, s>>>(
+        in, n_in, out, src, n_new, err);
+    const int64_t per_cta_small = (int64_t)kThreads * kGatherSmallU;
+    gather_small_kernel<<<(unsigned)((7 * (int64_t)n_new + per_cta_small - 1) / per_cta_small), kThreads, 0, s>>>(
+        in, n_in, out, src, n_new);
     return cudaGetLastError();
 }
 
