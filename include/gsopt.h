@@ -262,7 +262,7 @@ int64_t gs_opt_rows(const gs_opt *opt);
  *   mask         device [n_rows] uint8 out: 1 visible, 0 not.  Required.
  *   visible_rows device [n_rows] int32 out, optional (NULL): the visible row
  *                indices, compacted (ascending within each tile of rows,
- *                tiles in completion order; a tile is 1024 rows when xyz is
+ *                tiles in completion order; a tile is 2048 rows when xyz is
  *                16-B and mask 4-B aligned, else 256).
  *   n_visible    device int64 out, optional (NULL): the visible count; required
  *                when visible_rows is given.
