@@ -41,30 +41,90 @@ def _scenes(prec_name, G):
     return runs_b, runs_s, cams
 
 
-@pytest.mark.parametrize("prec", ["FP32", "BF16_HYBRID", "FP16_BLOCK"])
-def test_batch_equals_single_scene_steps(G, prec):
-    runs_b, runs_s, cams = _scenes(prec, G)
-    b = G.gs_batch_create([r.h for r in runs_b])
-    nvis = torch.zeros(len(SIZES), dtype=torch.int64, device="cuda")
-    n_cand = {"FP32": 6, "BF16_HYBRID": 3, "FP16_BLOCK": 3}[prec]
-    steps = 3 * n_cand + 6                  # tuning, then the tuned eager and graph paths
-    for k in range(1, steps + 1):
-        for s, (rb, rs) in enumerate(zip(runs_b, runs_s)):
-            p = G.make_params(synth.lr_for_step(k, steps), k, restate=(k % 5 == 0), restate_ratio=0.3, seed=s)
-            cam = G.make_camera(cams[s][(k * 7 + s) % len(cams[s])])
-            b.set(s, G.make_attrs(rb.attrs), G.make_attrs(rb.grads), cam, p)
-            rs.step_camera(cams[s][(k * 7 + s) % len(cams[s])], p, mask_out=False)
-            nvis[s] -= rs.nvis[0]
-        G.gs_batch_step(b, nvis, graph=(k > 3 * n_cand + 3))
+def _step_both(G, b, runs_b, runs_s, cams, nvis, k, total, graph):
+    for s, (rb, rs) in enumerate(zip(runs_b, runs_s)):
+        p = G.make_params(synth.lr_for_step(k, total), k, restate=(k % 5 == 0), restate_ratio=0.3, seed=s)
+        cam = cams[s][(k * 7 + s) % len(cams[s])]
+        b.set(s, G.make_attrs(rb.attrs), G.make_attrs(rb.grads), G.make_camera(cam), p)
+        rs.step_camera(cam, p, mask_out=False)
+        nvis[s] -= rs.nvis[0]
+    G.gs_batch_step(b, nvis, graph=graph)
+
+
+def _assert_same(runs_b, runs_s, nvis):
     torch.cuda.synchronize()
-    cfg = G.gs_batch_config(b)
-    assert cfg["tuned"]
     assert int(nvis.abs().sum().item()) == 0          # same visible counts
     for rb, rs in zip(runs_b, runs_s):
         assert rb.rows().tobytes() == rs.rows().tobytes()
         mb, vb, tb = rb.state()
         ms, vs, ts = rs.state()
         assert mb.tobytes() == ms.tobytes() and vb.tobytes() == vs.tobytes() and tb.tobytes() == ts.tobytes()
+
+
+@pytest.mark.parametrize("prec", ["FP32", "BF16_HYBRID", "FP16_BLOCK"])
+def test_batch_equals_single_scene_steps(G, prec):
+    """Eager calls until the tuner has run every candidate (each candidate in
+    turn), then tuned eager calls, then graph replays."""
+    runs_b, runs_s, cams = _scenes(prec, G)
+    b = G.gs_batch_create([r.h for r in runs_b])
+    nvis = torch.zeros(len(SIZES), dtype=torch.int64, device="cuda")
+    total, k = 60, 0
+    while not G.gs_batch_config(b)["tuned"]:
+        k += 1
+        assert k <= 40, "tuning did not finish"
+        _step_both(G, b, runs_b, runs_s, cams, nvis, k, total, graph=False)
+    for _ in range(3):
+        k += 1
+        _step_both(G, b, runs_b, runs_s, cams, nvis, k, total, graph=False)
+    for _ in range(3):
+        k += 1
+        _step_both(G, b, runs_b, runs_s, cams, nvis, k, total, graph=True)
+    _assert_same(runs_b, runs_s, nvis)
+    b.close()
+    for r in runs_b + runs_s:
+        r.close()
+
+
+def _grow(G, run, n_add, seed):
+    """Re-index a scene to n + n_add rows: the old rows keep their state, the
+    new ones start fresh and copy the attributes of random old rows."""
+    n = run.n
+    rng = np.random.default_rng(seed)
+    src = np.concatenate([np.arange(n), np.full(n_add, -1)]).astype(np.int32)
+    attr_src = np.concatenate([np.arange(n), rng.integers(0, n, n_add)]).astype(np.int32)
+    G.gs_reindex_state(run.h, torch.from_numpy(src).cuda(), None, src.size)
+    out = {k: torch.empty((src.size,) + tuple(v.shape[1:]), dtype=v.dtype, device="cuda") for k, v in run.attrs.items()}
+    G.gs_gather_attrs(run.h, G.make_attrs(run.attrs), n, G.make_attrs(out), torch.from_numpy(attr_src).cuda(), src.size)
+    grads = {k: torch.zeros_like(v) for k, v in out.items()}
+    for k, v in run.grads.items():
+        grads[k][:n].copy_(v)
+        grads[k][n:].copy_(v[torch.from_numpy(attr_src[n:]).cuda().long()])
+    run.attrs, run.grads, run.n = out, grads, src.size
+
+
+def test_batch_graph_follows_scene_sizes(G):
+    """Graph replays, then one scene grows by a re-index (its tile count
+    changes, and with it the batch's tile table and, for the one-CTA-per-tile
+    form, the grid of the graph's kernel), then more graph replays: still
+    bit-identical to single-scene steps."""
+    runs_b, runs_s, cams = _scenes("FP32", G)
+    b = G.gs_batch_create([r.h for r in runs_b])
+    nvis = torch.zeros(len(SIZES), dtype=torch.int64, device="cuda")
+    total, k = 60, 0
+    while not G.gs_batch_config(b)["tuned"]:
+        k += 1
+        assert k <= 40, "tuning did not finish"
+        _step_both(G, b, runs_b, runs_s, cams, nvis, k, total, graph=False)
+    for _ in range(3):
+        k += 1
+        _step_both(G, b, runs_b, runs_s, cams, nvis, k, total, graph=True)
+    for run in (runs_b[3], runs_s[3]):
+        _grow(G, run, 20_011, 1250)
+    for _ in range(4):
+        k += 1
+        _step_both(G, b, runs_b, runs_s, cams, nvis, k, total, graph=True)
+    _assert_same(runs_b, runs_s, nvis)
+    assert runs_b[3].n == SIZES[3] + 20_011
     b.close()
     for r in runs_b + runs_s:
         r.close()
