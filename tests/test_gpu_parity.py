@@ -320,6 +320,25 @@ def test_multi_step_parity_small(G, orc):
     print("ambiguous decisions:", amb, group_errors(got, ref.st.theta, rows=keep))
 
 
+@pytest.mark.parametrize("method", ["sparse_adam", "adamw_gs"])
+def test_c1_full_workload(G, orc, method):
+    """The 100 k-primitive, 50-step workload, every row against the oracle:
+    plain Sparse Adam (no DAR, no RSR) and AdamW-GS (DAR every step, RSR
+    every 25 steps so that two re-state events fall inside the run)."""
+    import dataclasses
+    wl = synth.WORKLOADS["c1_100k"]
+    if method == "sparse_adam":
+        wl = dataclasses.replace(wl, dar=False, restate_every=10 ** 9)
+    else:
+        wl = dataclasses.replace(wl, restate_every=25, restate_ratio=0.3)
+    got, ref, t, keep, amb = _run_sequence(G, orc, wl, wl.steps)
+    assert keep.mean() > 0.999
+    errs = assert_close(got, ref.st.theta, 1e-4, rows=keep, what=f"{method}, {wl.steps} steps")
+    assert np.array_equal(t[keep], ref.st.t[keep])
+    assert (t > 0).mean() > 0.5                  # most rows were visible at some step
+    print(method, "ambiguous decisions:", amb, errs)
+
+
 def test_full_size_1000_steps_sampled(G, orc):
     """The 1 M-primitive, 1000-step workload in the launch configuration the
     bench times, checked on 3000 sampled primitives the oracle follows."""
