@@ -636,8 +636,12 @@ def next_rows_leg(G, synth, steps, warmup=10, aiu_prob=0.1):
         r = timed_run(G, sc, "fp32", steps, warmup, extra=extra)
         inv = wl.n - r["nv"] / steps
         byt = r["bytes_per_launch"] + inv * (b_inv + b_aiu)
+        gbs = byt / r["step_s"] / 1e9
         out[name] = {"value": r["nv"] / r["elapsed"], "ms_per_step": r["elapsed"] / steps * 1e3,
-                     "hbm_gbs": byt / r["step_s"] / 1e9, "slowdown_vs_plain": r["step_s"] / base["step_s"]}
+                     "hbm_gbs": gbs, "slowdown_vs_plain": r["step_s"] / base["step_s"],
+                     # time per algorithmic byte against the plain step: the terms that read
+                     # invisible rows (noise on every row, AIU) move more bytes per step
+                     "slowdown_per_byte_vs_plain": out["plain"]["hbm_gbs"] / gbs}
     del sc
     torch.cuda.empty_cache()
     # prune list over 6 M logits

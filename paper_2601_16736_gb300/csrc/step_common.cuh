@@ -406,9 +406,11 @@ struct State<GS_MOM_FP16_BLOCK> {
 // values at kF16BRot, exponent 6), c = 13 xyz + scale + opacity (7 values at
 // kF16BXso, exponent 7) with the step count t (uint16, saturating) in the
 // high half of the fourth word.  The visible update as small_item; RSR
-// scales the moments afterwards.
-__device__ __forceinline__ void small_item_f16b(const StepArgs &a, const int32_t row, const int c, const bool sampled,
-                                                const float2 f)
+// scales the moments afterwards.  kX: item 13 subtracts the row's noise nz
+// from xyz and returns whether the row is active after the step.
+template <bool kX>
+__device__ __forceinline__ bool small_item_f16b(const StepArgs &a, const int32_t row, const int c, const bool sampled,
+                                                const float2 f, const float3 nz)
 {
     using S = State<GS_MOM_FP16_BLOCK>;
     char *mr = S::row(a.m, row), *vr = S::row(a.v, row);
@@ -441,6 +443,7 @@ __device__ __forceinline__ void small_item_f16b(const StepArgs &a, const int32_t
         __stcs(reinterpret_cast<uint2 *>(vr + kF16BRot), make_uint2(hv[0], hv[1]));
         mr[kF16BExp + 6] = (char)em;
         vr[kF16BExp + 6] = (char)ev;
+        return false;
     } else {
         const uint4 um = *reinterpret_cast<const uint4 *>(mr + kF16BXso), uv = *reinterpret_cast<const uint4 *>(vr + kF16BXso);
         const uint32_t wm[4] = {um.x, um.y, um.z, um.w & 0xffffu}, wv[4] = {uv.x, uv.y, uv.z, uv.w};
@@ -464,6 +467,9 @@ __device__ __forceinline__ void small_item_f16b(const StepArgs &a, const int32_t
         s1 = step_element(s1, gs1, m[4], v[4], f.x, f.y, a, a.lr[1], ds, r1s, a.lam_s, a.clip_s);
         s2 = step_element(s2, gs2, m[5], v[5], f.x, f.y, a, a.lr[1], ds, r2s, a.lam_s, a.clip_s);
         op = step_element(op, go, m[6], v[6], f.x, f.y, a, a.lr[3], dop, rop, a.lam_o, a.clip_o);
+        if constexpr (kX) {
+            x0 -= nz.x; x1 -= nz.y; x2 -= nz.z;
+        }
         __stcs(px, x0); __stcs(px + 1, x1); __stcs(px + 2, x2);
         __stcs(ps, s0); __stcs(ps + 1, s1); __stcs(ps + 2, s2);
         __stcs(po, op);
@@ -481,6 +487,7 @@ __device__ __forceinline__ void small_item_f16b(const StepArgs &a, const int32_t
         __stcs(reinterpret_cast<uint4 *>(vr + kF16BXso), make_uint4(hv[0], hv[1], hv[2], hv[3]));
         mr[kF16BExp + 7] = (char)em;
         vr[kF16BExp + 7] = (char)ev;
+        return kX && op > a.tau_act;
     }
 }
 
@@ -573,6 +580,26 @@ inline int resident_ctas(const void *fn, int *cache)
 }
 
 // Prefetch when at most 60 % of the tile's rows are visible.
+// Beside the means: ask L2 for what phase A of the tile one wave ahead reads
+// for its rows, so that its loads find them on chip: the opacity logits when
+// counting N_a or drawing noise, and the rotations and log-scales for noise.
+// A hint only; whole tiles, 16-B aligned sources.
+template <int kTile>
+__device__ __forceinline__ void prefetch_tile_ahead_x(const StepArgs &a)
+{
+    if (threadIdx.x != 0 || a.tile_ahead <= 0 || !(a.n_active || a.noise)) return;
+    const int64_t q = ((int64_t)blockIdx.x + a.tile_ahead) * kTile;
+    if (q + kTile > (int64_t)a.n_rows) return;
+    if (((uintptr_t)a.a_op & 15u) == 0)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.a_op + q), "n"(kTile * 4) : "memory");
+    if (a.noise) {
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.a_rot + q * 4), "n"(kTile * 16) : "memory");
+        if (((uintptr_t)a.a_scale & 15u) == 0)
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.a_scale + q * 3), "n"(kTile * 12)
+                         : "memory");
+    }
+}
+
 template <int kTile>
 __device__ __forceinline__ bool sparse_tile(int nv) { return 5 * nv <= 3 * kTile; }
 
@@ -659,15 +686,60 @@ __device__ __forceinline__ void sh_item(const StepArgs &a, const int32_t row, co
     S::template store_sh<kW>(a, row, i, m, v, t);
 }
 
+// gamma ~ N(0, I_3) by the Box-Muller transform (Box & Muller 1958) on
+// 24-bit uniforms from two SplitMix64 words (stream tags 2 and 3):
+// ua = (w >> 40 + 1) / 2^24 in (0, 1], ub = bits 16..39 / 2^24 in [0, 1).
+__device__ __forceinline__ float3 noise_gamma(const StepArgs &a, int32_t row)
+{
+    const uint64_t h1 = splitmix64_at(a.seed, draw_counter(2, a.k_ctr, row));
+    const uint64_t h2 = splitmix64_at(a.seed, draw_counter(3, a.k_ctr, row));
+    const float ua1 = (float)((h1 >> 40) + 1ull) * 0x1p-24f, ub1 = (float)((h1 >> 16) & 0xFFFFFFull) * 0x1p-24f;
+    const float ua2 = (float)((h2 >> 40) + 1ull) * 0x1p-24f, ub2 = (float)((h2 >> 16) & 0xFFFFFFull) * 0x1p-24f;
+    const float r1 = sqrtf(-2.f * logf(ua1)), r2 = sqrtf(-2.f * logf(ua2));
+    float s1, c1;
+    sincospif(2.f * ub1, &s1, &c1);
+    return make_float3(r1 * c1, r1 * s1, r2 * cospif(2.f * ub2));
+}
+
+// Position noise of one primitive from its values before this step (App.
+// Eq. disentangled_mu): the amount subtracted from mu,
+//   eta_Ro * eta_mu * sigmoid(-lambda_mu (o - lambda_t)) * Sigma gamma,
+// Sigma = R diag(exp(2 kappa)) R^T, R the rotation of the normalised
+// quaternion q = (w, x, y, z).  Sigma gamma is formed as R (s^2 .* (R^T gamma)).
+__device__ __forceinline__ float3 noise_term(const StepArgs &a, int32_t row, float4 q, float k0, float k1, float k2,
+                                             float tau)
+{
+    const float o = 1.f / (1.f + expf(-tau));
+    const float gate = 1.f / (1.f + expf(a.noise_k * (o - a.noise_t)));
+    const float c = a.noise_scale * gate;
+    if (c == 0.f) return make_float3(0.f, 0.f, 0.f);
+    const float3 g = noise_gamma(a, row);
+    const float nrm = fmaxf(sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w), 1e-12f);
+    const float w = q.x / nrm, x = q.y / nrm, y = q.z / nrm, z = q.w / nrm;
+    const float r00 = 1.f - 2.f * (y * y + z * z), r01 = 2.f * (x * y - w * z), r02 = 2.f * (x * z + w * y);
+    const float r10 = 2.f * (x * y + w * z), r11 = 1.f - 2.f * (x * x + z * z), r12 = 2.f * (y * z - w * x);
+    const float r20 = 2.f * (x * z - w * y), r21 = 2.f * (y * z + w * x), r22 = 1.f - 2.f * (x * x + y * y);
+    const float p0 = (r00 * g.x + r10 * g.y + r20 * g.z) * expf(2.f * k0);
+    const float p1 = (r01 * g.x + r11 * g.y + r21 * g.z) * expf(2.f * k1);
+    const float p2 = (r02 * g.x + r12 * g.y + r22 * g.z) * expf(2.f * k2);
+    return make_float3(c * (r00 * p0 + r01 * p1 + r02 * p2), c * (r10 * p0 + r11 * p1 + r12 * p2),
+                       c * (r20 * p0 + r21 * p1 + r22 * p2));
+}
+
 // Small item c of a visible row: 12 rotation, 13 xyz + scale0, 14 scale1 +
-// scale2 + opacity (+ t where the format keeps it there).
-template <int kPrec>
-__device__ __forceinline__ void small_item(const StepArgs &a, const int32_t row, const int c, const bool sampled,
-                                           const float2 f)
+// scale2 + opacity (+ t where the format keeps it there).  kX (the step with
+// the active count and/or noise on visible rows): the xyz item subtracts the
+// row's noise nz, and the opacity item returns whether the row is active
+// after the step (opacity logit above tau_act); otherwise nz is unused and
+// the result false.
+template <int kPrec, bool kX = false>
+__device__ __forceinline__ bool small_item(const StepArgs &a, const int32_t row, const int c, const bool sampled,
+                                           const float2 f, const float3 nz = float3{0.f, 0.f, 0.f})
 {
     if constexpr (kPrec == GS_MOM_FP16_BLOCK) {
-        small_item_f16b(a, row, c, sampled, f);
+        return small_item_f16b<kX>(a, row, c, sampled, f, nz);
     } else {
+        bool active = false;
         using S = State<kPrec>;
         Chunk k = S::load_small(a, row, c);
         float4 &m = k.m, &v = k.v;
@@ -697,6 +769,9 @@ __device__ __forceinline__ void small_item(const StepArgs &a, const int32_t row,
             x1 = step_element(x1, g1, m.y, v.y, f.x, f.y, a, a.lr[0], false, 0.f, 0.f, 0.f);
             x2 = step_element(x2, g2, m.z, v.z, f.x, f.y, a, a.lr[0], false, 0.f, 0.f, 0.f);
             s0 = step_element(s0, gs0, m.w, v.w, f.x, f.y, a, a.lr[1], ds, r0s, a.lam_s, a.clip_s);
+            if constexpr (kX) {
+                x0 -= nz.x; x1 -= nz.y; x2 -= nz.z;
+            }
             __stcs(px, x0); __stcs(px + 1, x1); __stcs(px + 2, x2);
             __stcs(ps, s0);
         } else {
@@ -716,6 +791,7 @@ __device__ __forceinline__ void small_item(const StepArgs &a, const int32_t row,
             __stcs(ps + 1, s1); __stcs(ps + 2, s2);
             __stcs(po, op);
             if (!S::kTInSh) k.t += 1u;         // the row's own step count (Sec. 3.2)
+            if constexpr (kX) active = op > a.tau_act;
         }
         if (sampled) {         // RSR post-scale (chunk 14 holds 3 moments)
             m.x *= a.alpha1; m.y *= a.alpha1; m.z *= a.alpha1;
@@ -723,6 +799,7 @@ __device__ __forceinline__ void small_item(const StepArgs &a, const int32_t row,
             if (c != 14) { m.w *= a.alpha1; v.w *= a.alpha2; }
         }
         S::store_small(a, row, c, k);
+        return active;
     }
 }
 

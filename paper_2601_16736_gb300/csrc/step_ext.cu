@@ -1,11 +1,13 @@
 // The step with its optional terms: position noise (App. Eq.
 // disentangled_mu), the Artificial Implicit Update of sampled invisible
 // primitives (Sec. 3.2), and the active count N_a (Sec. 4, opacity > 1/255).
-// Launched only when a step asks for one of them; the plain step kernel is
-// untouched by them.
+// Launched when a step asks for AIU or for noise on every row, the terms
+// that touch invisible rows; the count and noise on visible rows alone take
+// the terms form of the plain step kernel, and the plain step is untouched
+// by any of them.
 //
-// Per tile of 256 rows (one CTA of 256 threads, 4 CTAs per SM as the plain
-// step):
+// Per tile of 256 rows (one CTA of 256 threads; 5 CTAs per SM for FP32 and
+// BF16 moments, 4 for the others):
 //   A. visibility, StSS, AIU and noise decisions per row.  A row that takes
 //      the noise has it computed here, from its values before this step, and
 //      kept in shared memory; a noise-only invisible row is finished here.
@@ -20,46 +22,6 @@ namespace gs {
 namespace {
 
 constexpr uint8_t kFRsr = 1, kFAiu = 2, kFNoise = 4;
-
-// gamma ~ N(0, I_3) by the Box-Muller transform (Box & Muller 1958) on
-// 24-bit uniforms from two SplitMix64 words (stream tags 2 and 3):
-// ua = (w >> 40 + 1) / 2^24 in (0, 1], ub = bits 16..39 / 2^24 in [0, 1).
-__device__ __forceinline__ float3 noise_gamma(const StepArgs &a, int32_t row)
-{
-    const uint64_t h1 = splitmix64_at(a.seed, draw_counter(2, a.k_ctr, row));
-    const uint64_t h2 = splitmix64_at(a.seed, draw_counter(3, a.k_ctr, row));
-    const float ua1 = (float)((h1 >> 40) + 1ull) * 0x1p-24f, ub1 = (float)((h1 >> 16) & 0xFFFFFFull) * 0x1p-24f;
-    const float ua2 = (float)((h2 >> 40) + 1ull) * 0x1p-24f, ub2 = (float)((h2 >> 16) & 0xFFFFFFull) * 0x1p-24f;
-    const float r1 = sqrtf(-2.f * logf(ua1)), r2 = sqrtf(-2.f * logf(ua2));
-    float s1, c1;
-    sincospif(2.f * ub1, &s1, &c1);
-    return make_float3(r1 * c1, r1 * s1, r2 * cospif(2.f * ub2));
-}
-
-// Position noise of one primitive from its values before this step (App.
-// Eq. disentangled_mu): the amount subtracted from mu,
-//   eta_Ro * eta_mu * sigmoid(-lambda_mu (o - lambda_t)) * Sigma gamma,
-// Sigma = R diag(exp(2 kappa)) R^T, R the rotation of the normalised
-// quaternion q = (w, x, y, z).  Sigma gamma is formed as R (s^2 .* (R^T gamma)).
-__device__ __forceinline__ float3 noise_term(const StepArgs &a, int32_t row, float4 q, float k0, float k1, float k2,
-                                             float tau)
-{
-    const float o = 1.f / (1.f + expf(-tau));
-    const float gate = 1.f / (1.f + expf(a.noise_k * (o - a.noise_t)));
-    const float c = a.noise_scale * gate;
-    if (c == 0.f) return make_float3(0.f, 0.f, 0.f);
-    const float3 g = noise_gamma(a, row);
-    const float nrm = fmaxf(sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w), 1e-12f);
-    const float w = q.x / nrm, x = q.y / nrm, y = q.z / nrm, z = q.w / nrm;
-    const float r00 = 1.f - 2.f * (y * y + z * z), r01 = 2.f * (x * y - w * z), r02 = 2.f * (x * z + w * y);
-    const float r10 = 2.f * (x * y + w * z), r11 = 1.f - 2.f * (x * x + z * z), r12 = 2.f * (y * z - w * x);
-    const float r20 = 2.f * (x * z - w * y), r21 = 2.f * (y * z + w * x), r22 = 1.f - 2.f * (x * x + y * y);
-    const float p0 = (r00 * g.x + r10 * g.y + r20 * g.z) * expf(2.f * k0);
-    const float p1 = (r01 * g.x + r11 * g.y + r21 * g.z) * expf(2.f * k1);
-    const float p2 = (r02 * g.x + r12 * g.y + r22 * g.z) * expf(2.f * k2);
-    return make_float3(c * (r00 * p0 + r01 * p1 + r02 * p2), c * (r10 * p0 + r11 * p1 + r12 * p2),
-                       c * (r20 * p0 + r21 * p1 + r22 * p2));
-}
 
 // The AIU step of one value from unchanged moments: theta - lr m^/(sqrt(v^) + eps).
 __device__ __forceinline__ float aiu_element(float th, float m, float v, float2 f, float eps, float lr)
@@ -331,26 +293,6 @@ struct TileListsX {
 __device__ __forceinline__ float2 factors(const StepArgs &a, uint32_t k)
 {
     return k < (uint32_t)a.fac_len ? a.fac[k] : make_float2(1.0f, 1.0f);
-}
-
-// Beside the means: ask L2 for what phase A of the tile one wave ahead reads
-// for its rows, so that its loads find them on chip: the opacity logits when
-// counting N_a or drawing noise, and the rotations and log-scales for noise.
-// A hint only; whole tiles, 16-B aligned sources.
-template <int kTile>
-__device__ __forceinline__ void prefetch_tile_ahead_x(const StepArgs &a)
-{
-    if (threadIdx.x != 0 || a.tile_ahead <= 0 || !(a.n_active || a.noise)) return;
-    const int64_t q = ((int64_t)blockIdx.x + a.tile_ahead) * kTile;
-    if (q + kTile > (int64_t)a.n_rows) return;
-    if (((uintptr_t)a.a_op & 15u) == 0)
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.a_op + q), "n"(kTile * 4) : "memory");
-    if (a.noise) {
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.a_rot + q * 4), "n"(kTile * 16) : "memory");
-        if (((uintptr_t)a.a_scale & 15u) == 0)
-            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.a_scale + q * 3), "n"(kTile * 12)
-                         : "memory");
-    }
 }
 
 // Phase A of the extended step; returns the two list lengths.

@@ -36,14 +36,30 @@ struct TileLists {
     int32_t cnt[2][kTile / 32];
 };
 
+// What the step with the active count and/or position noise on its visible
+// rows (the terms form, kX) keeps beside the lists: for each listed visible
+// row, the values its noise is drawn from as they were before the step
+// (quaternion; log-scales and opacity logit), read in phase A, and the
+// tile's count of rows active after the step.  The xyz item draws the noise
+// from the kept values, so the items that update the rotation, scale and
+// opacity cannot change its inputs, and the draw runs on converged warps.
+template <int kTile>
+struct TileTerms {
+    float4 q[kTile];
+    float4 sko[kTile];        // kappa 0-2, tau
+    unsigned active;
+};
+
 // Decide visibility and StSS membership for the tile's rows, prefetch the
 // step counters of visible rows (at byte kTByte of their m row), and compact
 // both row sets into `L`; in a sparse tile, ask L2 for each visible row's
 // data.  Returns the visible count in nv and the invisible-sampled count in
-// nr.
-template <int kTile, int kRowBytes, int kTByte>
+// nr.  kX: the inputs of a visible row's noise (App. Eq. disentangled_mu)
+// go to X beside its list entry, and invisible rows, whose opacity this step
+// leaves unchanged, are counted into X->active when the step counts N_a.
+template <int kTile, int kRowBytes, int kTByte, bool kX>
 __device__ __forceinline__ void tile_decide(const StepArgs &a, const int vis_src, const int64_t r0, TileLists<kTile> &L,
-                                            int &nv, int &nr)
+                                            TileTerms<kTile> *X, int &nv, int &nr)
 {
     constexpr int kRpt = kTile / kThreads;
     constexpr int kWarps = kThreads / 32;
@@ -51,6 +67,11 @@ __device__ __forceinline__ void tile_decide(const StepArgs &a, const int vis_src
     const int nrow = (int)min((int64_t)kTile, (int64_t)a.n_rows - r0);
     unsigned bal_v[kRpt], bal_r[kRpt], bal_s[kRpt];
     uint32_t t_old[kRpt];
+    float4 xq[kX ? kRpt : 1], xs[kX ? kRpt : 1];
+    unsigned my_active = 0;
+    if constexpr (kX) {
+        if (tid == 0) X->active = 0u;
+    }
 #pragma unroll
     for (int j = 0; j < kRpt; ++j) {
         const int lr = j * kThreads + tid;
@@ -75,6 +96,14 @@ __device__ __forceinline__ void tile_decide(const StepArgs &a, const int vis_src
             if (a.mask_out) a.mask_out[row] = vis ? 1 : 0;
             if (a.restate) smp = stss_sampled(a, (int32_t)row);
         }
+        if constexpr (kX) {
+            if (in && vis && a.noise) {
+                xq[j] = ld4(a.a_rot + row * 4);
+                const float *ps = a.a_scale + row * 3;
+                xs[j] = make_float4(ps[0], ps[1], ps[2], a.a_op[row]);
+            }
+            if (in && !vis && a.n_active) my_active += a.a_op[row] > a.tau_act ? 1u : 0u;
+        }
         bal_v[j] = __ballot_sync(0xffffffffu, vis);
         bal_s[j] = __ballot_sync(0xffffffffu, smp);
         bal_r[j] = bal_s[j] & ~bal_v[j];
@@ -84,6 +113,12 @@ __device__ __forceinline__ void tile_decide(const StepArgs &a, const int vis_src
         }
     }
     __syncthreads();
+    if constexpr (kX) {
+        if (a.n_active) {
+            my_active = __reduce_add_sync(0xffffffffu, my_active);
+            if (lane == 0 && my_active) atomicAdd(&X->active, my_active);
+        }
+    }
     nv = 0;
     nr = 0;
 #pragma unroll 4
@@ -108,6 +143,7 @@ __device__ __forceinline__ void tile_decide(const StepArgs &a, const int vis_src
             if (sparse_tile<kTile>(nv)) prefetch_row_l2<kRowBytes>(a, row);
             const uint32_t tb = a.bias_mode ? a.k_bias : t_old[j] + 1u;
             L.fac[pos] = (tb < (uint32_t)a.fac_len) ? a.fac[tb] : make_float2(1.0f, 1.0f);
+            if constexpr (kX) { if (a.noise) { X->q[pos] = xq[j]; X->sko[pos] = xs[j]; } }
         }
         if (bal_r[j] & (1u << lane)) L.rlist[br + __popc(bal_r[j] & lt)] = row;
     }
@@ -119,9 +155,12 @@ __device__ __forceinline__ void tile_decide(const StepArgs &a, const int vis_src
 
 // Phase B of one tile: the items of its visible and invisible-sampled rows
 // (nv, nr of them in L), grouped by kind: all SH items, then the small
-// items, then RSR.
-template <int kTile, int kPrec, int kW>
-__device__ __forceinline__ void tile_items(const StepArgs &a, const TileLists<kTile> &L, const int nv, const int nr)
+// items, then RSR.  kX: the xyz items draw the rows' noise from the values
+// kept in X and subtract it, the opacity items count the rows active after
+// the step, and the tile's count is added to a.n_active.
+template <int kTile, int kPrec, int kW, bool kX>
+__device__ __forceinline__ void tile_items(const StepArgs &a, const TileLists<kTile> &L, TileTerms<kTile> *X,
+                                           const int nv, const int nr)
 {
     constexpr int kNsh = 48 / kW, kItems = kNsh + kSmallItems<kPrec>;
     const int e_sh = kNsh * nv, e_vis = kItems * nv, e_all = e_vis + kItems * nr;
@@ -129,6 +168,7 @@ __device__ __forceinline__ void tile_items(const StepArgs &a, const TileLists<kT
     // items) with the same item-to-thread assignment as a single loop: the
     // kinds no longer share a loop body, so their register demands do not
     // add up (FP16 block then fits 5 CTAs per SM).
+    unsigned my_active = 0;
     int w = threadIdx.x;
     for (; w < e_sh; w += kThreads) {
         const int j = w / kNsh, i = w - j * kNsh;
@@ -139,26 +179,43 @@ __device__ __forceinline__ void tile_items(const StepArgs &a, const TileLists<kT
         const int q = w - e_sh;
         const int j = q % nv, c = 12 + q / nv;
         const int32_t e = L.list[j];
-        small_item<kPrec>(a, e & 0x7fffffff, c, e < 0, L.fac[j]);
+        if constexpr (kX) {
+            float3 nz = make_float3(0.f, 0.f, 0.f);
+            if (c == 13 && a.noise) {
+                const float4 q = X->q[j], s4 = X->sko[j];
+                nz = noise_term(a, e & 0x7fffffff, q, s4.x, s4.y, s4.z, s4.w);
+            }
+            my_active += small_item<kPrec, true>(a, e & 0x7fffffff, c, e < 0, L.fac[j], nz) ? 1u : 0u;
+        } else {
+            small_item<kPrec>(a, e & 0x7fffffff, c, e < 0, L.fac[j]);
+        }
     }
     for (; w < e_all; w += kThreads) {
         const int q = w - e_vis;
         const int j = q / kItems, i = q - j * kItems;
         rsr_item<kPrec, kW>(a, L.rlist[j], i);
     }
+    if constexpr (kX) {
+        if (a.n_active) {
+            my_active = __reduce_add_sync(0xffffffffu, my_active);
+            if ((threadIdx.x & 31) == 0 && my_active) atomicAdd(&X->active, my_active);
+            __syncthreads();
+            if (threadIdx.x == 0 && X->active) atomicAdd(a.n_active, (unsigned long long)X->active);
+        }
+    }
 }
 
 // One tile: phase A, then its items.
-template <int kTile, int kPrec, int kW>
+template <int kTile, int kPrec, int kW, bool kX = false>
 __device__ __forceinline__ void process_tile(const StepArgs &a, const int vis_src, const int64_t r0,
-                                             TileLists<kTile> &L)
+                                             TileLists<kTile> &L, TileTerms<kTile> *X = nullptr)
 {
     static_assert(kTile % kThreads == 0, "tile must be a multiple of the block");
     static_assert(kW == 4 || kW == 8, "SH items cover 4 or 8 columns");
     using S = State<kPrec>;
     int nv, nr;
-    tile_decide<kTile, S::kRowBytes, S::kTByte>(a, vis_src, r0, L, nv, nr);
-    tile_items<kTile, kPrec, kW>(a, L, nv, nr);
+    tile_decide<kTile, S::kRowBytes, S::kTByte, kX>(a, vis_src, r0, L, X, nv, nr);
+    tile_items<kTile, kPrec, kW, kX>(a, L, X, nv, nr);
 }
 
 template <int kTile, int kMinBlocks, int kPrec, int kW>
@@ -168,6 +225,20 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) step_tile(const StepArgs
     pdl_enter();
     prefetch_tile_ahead<kTile>(a, vis_src);
     process_tile<kTile, kPrec, kW>(a, vis_src, (int64_t)blockIdx.x * kTile, L);
+}
+
+// The terms form: the same step with the active count N_a (Sec. 4) and/or
+// position noise on the visible rows (App. Eq. disentangled_mu).  AIU and
+// noise on every row take the extended kernel instead.
+template <int kTile, int kMinBlocks, int kPrec, int kW>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) step_tile_terms(const StepArgs a, const int vis_src)
+{
+    __shared__ TileLists<kTile> L;
+    __shared__ TileTerms<kTile> X;
+    pdl_enter();
+    prefetch_tile_ahead<kTile>(a, vis_src);
+    prefetch_tile_ahead_x<kTile>(a);
+    process_tile<kTile, kPrec, kW, true>(a, vis_src, (int64_t)blockIdx.x * kTile, L, &X);
 }
 
 // Many scenes in one persistent launch.  The scene table lives in device
@@ -252,10 +323,16 @@ constexpr int kShWF32 = 4, kShWBf16 = 8;   // SH columns per item
 
 namespace {
 
-template <int kPrec, int kW>
+// Resident CTAs per SM of the terms form: 5 where it fits 48 registers
+// without spills (FP32, BF16), 4 for the hybrid and FP16-block formats.
+template <int kPrec>
+constexpr int kTermsMinBlocks = (kPrec == GS_MOM_FP32 || kPrec == GS_MOM_BF16) ? 5 : 4;
+
+template <int kPrec, int kW, bool kX>
 cudaError_t launch_tiles(const StepArgs &a, int vis_src, cudaStream_t s)
 {
-    auto k = step_tile<kStepTile, kStepMinBlocks<kPrec>, kPrec, kW>;
+    auto k = kX ? step_tile_terms<kStepTile, kTermsMinBlocks<kPrec>, kPrec, kW>
+                : step_tile<kStepTile, kStepMinBlocks<kPrec>, kPrec, kW>;
     static int s_res[64] = {};
     StepArgs b = a;
     b.tile_ahead = resident_ctas(reinterpret_cast<const void *>(k), s_res);
@@ -270,12 +347,21 @@ cudaError_t launch_step(const StepArgs &a, int prec, int vis_src, cudaStream_t s
     if (a.n_rows <= 0) return cudaSuccess;
     if (prec == GS_MOM_FP8E4M3)
         return (a.noise || a.aiu || a.n_active) ? cudaErrorNotSupported : launch_step_fp8(a, vis_src, s);
-    if (a.noise || a.aiu || a.n_active) return launch_step_ext(a, prec, vis_src, s);
+    if (a.aiu || a.noise == GS_NOISE_ALL) return launch_step_ext(a, prec, vis_src, s);
+    const bool x = a.n_active || a.noise;      // the count and/or noise on visible rows: the terms form
     switch (prec) {
-    case GS_MOM_FP32: return launch_tiles<GS_MOM_FP32, kShWF32>(a, vis_src, s);
-    case GS_MOM_BF16: return launch_tiles<GS_MOM_BF16, kShWBf16>(a, vis_src, s);
-    case GS_MOM_BF16_HYBRID: return launch_tiles<GS_MOM_BF16_HYBRID, kShWBf16>(a, vis_src, s);
-    case GS_MOM_FP16_BLOCK: return launch_tiles<GS_MOM_FP16_BLOCK, 8>(a, vis_src, s);
+    case GS_MOM_FP32:
+        return x ? launch_tiles<GS_MOM_FP32, kShWF32, true>(a, vis_src, s)
+                 : launch_tiles<GS_MOM_FP32, kShWF32, false>(a, vis_src, s);
+    case GS_MOM_BF16:
+        return x ? launch_tiles<GS_MOM_BF16, kShWBf16, true>(a, vis_src, s)
+                 : launch_tiles<GS_MOM_BF16, kShWBf16, false>(a, vis_src, s);
+    case GS_MOM_BF16_HYBRID:
+        return x ? launch_tiles<GS_MOM_BF16_HYBRID, kShWBf16, true>(a, vis_src, s)
+                 : launch_tiles<GS_MOM_BF16_HYBRID, kShWBf16, false>(a, vis_src, s);
+    case GS_MOM_FP16_BLOCK:
+        return x ? launch_tiles<GS_MOM_FP16_BLOCK, 8, true>(a, vis_src, s)
+                 : launch_tiles<GS_MOM_FP16_BLOCK, 8, false>(a, vis_src, s);
     default: return cudaErrorNotSupported;
     }
 }

@@ -50,27 +50,38 @@ def _ext(G, orc, **kw):
                       noise_t=o["noise_t"], aiu_prob=o["aiu_prob"], aiu_scale=o["aiu_scale"])
 
 
-def test_extended_kernel_without_terms_is_the_plain_step(G):
-    """Only the active count requested: the extended kernel must give the
-    plain kernel's results bit for bit (same per-element arithmetic)."""
+@pytest.mark.parametrize("prec", ["FP32", "BF16_HYBRID", "FP16_BLOCK"])
+def test_term_kernels_without_terms_are_the_plain_step(G, prec):
+    """The terms form of the step kernel (active count only) and the extended
+    kernel (noise on every row with eta_Ro = 0, so the noise is exactly zero,
+    plus the count) must give the plain kernel's results bit for bit: the
+    same per-element arithmetic.  Their counts must agree."""
     n = 20_011
     groups = synth.scene_uniform(n, 1900)
-    a = GpuScene(groups)
-    b = GpuScene(groups)
-    na = torch.zeros(1, dtype=torch.int64, device="cuda")
+    pr = getattr(G, "GS_MOM_" + prec)
+    a, b, c = GpuScene(groups, prec=pr), GpuScene(groups, prec=pr), GpuScene(groups, prec=pr)
+    nb = torch.zeros(1, dtype=torch.int64, device="cuda")
+    nc = torch.zeros(1, dtype=torch.int64, device="cuda")
     rng = np.random.default_rng(1901)
     for k in range(1, 6):
         g = synth.grads_rows(n, 1902, k)
         mask = torch.from_numpy((rng.random(n) < 0.5).astype(np.uint8)).cuda()
-        a.set_grads(g)
-        b.set_grads(g)
-        a.step_mask(mask, G.make_params(LR, k, restate=(k == 3), restate_ratio=0.4, seed=5))
-        b.step_mask(mask, G.make_params(LR, k, restate=(k == 3), restate_ratio=0.4, seed=5, n_active=na))
-    assert a.rows().tobytes() == b.rows().tobytes()
-    for x, y in zip(a.state(), b.state()):
-        assert x.tobytes() == y.tobytes()
-    a.close()
-    b.close()
+        for r in (a, b, c):
+            r.set_grads(g)
+        kw = dict(restate=(k == 3), restate_ratio=0.4, seed=5)
+        nb.zero_()
+        nc.zero_()
+        a.step_mask(mask, G.make_params(LR, k, **kw))
+        b.step_mask(mask, G.make_params(LR, k, n_active=nb, **kw))
+        c.step_mask(mask, G.make_params(LR, k, n_active=nc, noise=2, noise_lr=0.0, **kw))
+        torch.cuda.synchronize()
+        assert nb.item() == nc.item() > 0
+    ra = a.rows().tobytes()
+    assert b.rows().tobytes() == ra and c.rows().tobytes() == ra
+    for x, y, z in zip(a.state(), b.state(), c.state()):
+        assert x.tobytes() == y.tobytes() == z.tobytes()
+    for r in (a, b, c):
+        r.close()
 
 
 @pytest.mark.parametrize("prec", ["FP32", "BF16_HYBRID", "FP16_BLOCK"])
