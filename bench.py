@@ -283,8 +283,13 @@ def timed_run(G, sc, prec, steps, warmup, clocks_device=None, dist=None, extra=N
             rsr_steps.append(k)
             rsr += int(round(sc.wl.restate_ratio * (sc.wl.n - int(nv[warmup + j]))))
     byt = (timed_nv * bytes_visible(prec) + steps * sc.wl.n * BYTES_ROW_VIS + rsr * STATE_RW[prec]) / steps
+    # the first timed launch: the one an ncu capture skipping the warm-up launches (-s warmup -c 1) takes
+    k1, nv1 = sc.k(warmup), int(nv[warmup])
+    rsr1 = int(round(sc.wl.restate_ratio * (sc.wl.n - nv1))) if k1 % sc.wl.restate_every == 0 else 0
+    first = dict(iteration=k1, visible_rows=nv1, rsr_rows=rsr1,
+                 algorithmic_bytes=nv1 * bytes_visible(prec) + sc.wl.n * BYTES_ROW_VIS + rsr1 * STATE_RW[prec])
     out = dict(elapsed=elapsed, step_s=elapsed / steps, nv=timed_nv, bytes_per_launch=byt, clocks=clocks,
-               steps=steps, rsr_steps=rsr_steps, rsr_rows=rsr)
+               steps=steps, rsr_steps=rsr_steps, rsr_rows=rsr, first_timed=first)
     if instrument:
         _, _, per, _ = run(True)
         out["kern"] = float(per.mean())
@@ -447,7 +452,8 @@ def run_ours(args):
                      "traffic_source": traffic_note,
                      "bytes_per_launch": r["bytes_per_launch"],
                      "duration": "mean launch time in the timed region (region events / launches, back to back)",
-                     "step_ms": r["step_s"] * 1e3, "kernel_ms_isolated": r["kern"] * 1e3},
+                     "step_ms": r["step_s"] * 1e3, "kernel_ms_isolated": r["kern"] * 1e3,
+                     "first_timed_launch": r["first_timed"]},
         "gpu_launches": args.steps,
         "clocks": r["clocks"],
     }
