@@ -8,20 +8,28 @@
 // slot that is zero throughout the block).  A value is code x scale.
 //
 // A block's scale is a power of two that keeps the largest magnitude of its
-// slot within e4m3's finite range (448): it grows at once when the values
-// need it, and shrinks only when the smallest fitting power of two is two
-// binades or more below it (import sets that smallest one).  Sparse Adam
-// updates only the visible rows of a block, but the scale belongs to all
-// 256, so one CTA takes one block, with its codes staged in shared memory:
-//   0. the largest code magnitude per column over the rows that stay as they
-//      are (a bytewise integer max: e4m3 magnitudes order as their codes);
-//   1. the new values of the rows that change (visible rows: the update;
-//      StSS-sampled rows: the RSR scaling), into the column maxima;
-//   2. the new scales, then the same values again: attributes written for
-//      visible rows, the changed values encoded with the new scales (m to
-//      nearest, v stochastically, a positive v never to zero);
-//   3. the kept rows re-encoded in the columns whose scale moved.
-// All arithmetic is FP32 (the step_element of the other formats).
+// slot within e4m3's finite range (448).  Sparse Adam updates only the
+// visible rows of a block, but the scale belongs to all 256, so one CTA
+// takes one block, in one of two ways:
+//   * on most steps the scales may only grow (f8_block_grow): only the rows
+//     that change are read and written, straight from and to device memory,
+//     and a column whose new values no longer fit takes a larger power of
+//     two, with the block's other rows re-encoded in that column alone;
+//   * on one step in kF8FullEvery (staggered over the blocks: iteration +
+//     block a multiple of it) the block's full pass recomputes every scale
+//     from all 256 rows, staged in shared memory, and shrinks it when the
+//     smallest fitting power of two is two binades or more below it:
+//       0. the largest code magnitude per column over the rows that stay as
+//          they are (a bytewise integer max: e4m3 magnitudes order as their
+//          codes);
+//       1. the new values of the rows that change (visible rows: the update;
+//          StSS-sampled rows: the RSR scaling), into the column maxima;
+//       2. the new scales, then the same values again: attributes written
+//          for visible rows, the changed values encoded with the new scales;
+//       3. the kept rows re-encoded in the columns whose scale moved.
+// m rounds to nearest, v stochastically, and a positive v never becomes
+// zero; import sets the smallest fitting scales.  All arithmetic is FP32
+// (the step_element of the other formats).
 
 #include <cuda_fp8.h>
 
@@ -35,6 +43,10 @@ constexpr int kF8Cols = 59;
 constexpr int kF8Row = 64;                   // bytes per code row
 constexpr int kF8TWord = 15;                 // 32-bit word of the m row holding t
 constexpr int kF8MinBlocks = 4;
+// A block recomputes its scales from all of its rows (and may shrink them)
+// on one step in kF8FullEvery, staggered over the blocks; on the others
+// they may only grow.
+constexpr uint32_t kF8FullEvery = 128;
 static_assert(kF8Tile == kThreads, "one row per thread in phase A");
 
 __device__ __forceinline__ float f8_dec(uint32_t code)
@@ -202,25 +214,205 @@ __device__ __forceinline__ void f8_apply_chunk(const StepArgs &a, const int k, c
     }
 }
 
-template <int kMinBlocks>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) step_fp8(const StepArgs a, const int vis_src)
+// Shared arrays of a block on a grow-only step.
+struct F8GrowShared {
+    __align__(16) float s_old[2][64], s_inv[2][64];
+    uint32_t s_max[2][64];
+    uint8_t flg[kF8Tile];                     // bit 0 visible, bit 1 StSS-sampled
+    int16_t clist[kF8Tile];                   // rows that change
+    float2 fac[kF8Tile];
+    uint16_t dmask[kF8Tile];                  // per row: the chunks deferred to pass 2
+    uint16_t dlist[kF8Tile * kF8Chunks];      // deferred chunks: list index << 4 | chunk
+    int nv, nc, nd, moved;
+    uint8_t mov[2 * 64];                      // moment << 6 | slot
+};
+
+// A block on a step where its scales may only grow (all but one step in
+// kF8FullEvery; the full pass recomputes them from every row and may shrink
+// them).  Only the rows that change are read, straight from and to device
+// memory, in one pass: a chunk whose new moments fit the range of the
+// current scales (448 s) is stored at once; a chunk with a value outside it
+// is left as it was and listed.  A column with such a value then takes the
+// smallest power of two that fits it (twice that when the column already
+// had a scale, so that a moment still rising does not move it again on the
+// next steps; the full pass keeps a scale up to two binades above the
+// smallest fitting), the block's other chunks are re-encoded in that column,
+// byte by byte in place (a changed row's new value is then rounded twice),
+// and the listed chunks are updated from their stored moments and encoded
+// under the grown scales.
+__device__ __forceinline__ void f8_block_grow(const StepArgs &a, const int vis_src, const int tile, const int nrow,
+                                              F8GrowShared &S)
+{
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int64_t r0 = (int64_t)tile * kF8Tile;
+    uint8_t *gm = static_cast<uint8_t *>(a.m), *gv = static_cast<uint8_t *>(a.v);
+    if (tid < 64) {
+        const float sm = tid < kF8Cols ? a.msc[tile * 64 + tid] : 0.f;
+        const float sv = tid < kF8Cols ? a.vsc[tile * 64 + tid] : 0.f;
+        S.s_old[0][tid] = sm;
+        S.s_old[1][tid] = sv;
+        S.s_inv[0][tid] = sm > 0.f ? __frcp_rn(sm) : 0.f;     // exact: powers of two
+        S.s_inv[1][tid] = sv > 0.f ? __frcp_rn(sv) : 0.f;
+        S.s_max[0][tid] = S.s_max[1][tid] = 0u;
+    }
+    if (tid == 0) S.nv = S.nc = S.nd = S.moved = 0;
+    if (tid < kF8Tile) S.dmask[tid] = 0;
+    const int64_t row = r0 + tid;
+    bool vis = false, smp = false;
+    uint32_t t_old = 0;
+    if (tid < nrow) {
+        if (vis_src == kVisCamera) {
+            const float *p = a.a_xyz + row * 3;
+            vis = frustum_visible(p[0], p[1], p[2], a.cam);
+        } else if (vis_src == kVisMask) {
+            vis = a.mask_in[row] != 0;
+        } else {
+            vis = true;
+        }
+        if (vis) t_old = reinterpret_cast<const uint32_t *>(gm + row * kF8Row)[kF8TWord];
+        if (a.mask_out) a.mask_out[row] = vis ? 1 : 0;
+        if (a.restate) smp = stss_sampled(a, (int32_t)row);
+    }
+    const unsigned bal_v = __ballot_sync(0xffffffffu, vis), bal_c = __ballot_sync(0xffffffffu, vis || smp);
+    __syncthreads();                          // scales and counters ready
+    if (lane == 0 && bal_v) atomicAdd(&S.nv, __popc(bal_v));
+    int base = 0;
+    if (lane == 0 && bal_c) base = atomicAdd(&S.nc, __popc(bal_c));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (vis || smp) S.clist[base + __popc(bal_c & ((1u << lane) - 1u))] = (int16_t)tid;
+    if (tid < nrow) {
+        const uint32_t tb = a.bias_mode ? a.k_bias : t_old + 1u;
+        S.fac[tid] = (vis && tb < (uint32_t)a.fac_len) ? a.fac[tb] : make_float2(1.0f, 1.0f);
+        S.flg[tid] = (vis ? 1 : 0) | (smp ? 2 : 0);
+    }
+    __syncthreads();
+    if (tid == 0 && a.n_visible && S.nv) atomicAdd(a.n_visible, (unsigned long long)S.nv);
+    const int nc = S.nc, e_sh = 12 * nc, total = kF8Chunks * nc;
+    // one pass over the changed rows' chunks
+    for (int w = tid; w < total; w += kThreads) {
+        int j, k;
+        if (w < e_sh) { j = w / 12; k = w - 12 * j; }
+        else { const int q = w - e_sh; k = 12 + q / nc; j = q - (k - 12) * nc; }
+        const int lr = S.clist[j], fl = S.flg[lr];
+        const int64_t r = r0 + lr;
+        float th[4], g[4], m[4], v[4];
+        if (fl & 1) f8_load_chunk(a, r, k, th, g);
+        uint32_t *pm = reinterpret_cast<uint32_t *>(gm + r * kF8Row) + k;
+        uint32_t *pv = reinterpret_cast<uint32_t *>(gv + r * kF8Row) + k;
+        f8_dec4(*pm, &S.s_old[0][4 * k], m);
+        f8_dec4(*pv, &S.s_old[1][4 * k], v);
+        f8_apply_chunk(a, k, fl & 1, fl & 2, S.fac[lr], th, g, m, v);
+        const int n = k == 14 ? 3 : 4;
+        bool out = false;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            if (e >= n) break;
+            const int c = 4 * k + e;
+            if (fabsf(m[e]) > 448.f * S.s_old[0][c]) { atomicMax(&S.s_max[0][c], __float_as_uint(fabsf(m[e]))); out = true; }
+            if (fabsf(v[e]) > 448.f * S.s_old[1][c]) { atomicMax(&S.s_max[1][c], __float_as_uint(fabsf(v[e]))); out = true; }
+        }
+        if (out) {                            // stored as it was; pass 2 redoes it
+            S.dlist[atomicAdd(&S.nd, 1)] = (uint16_t)(j << 4 | k);
+            atomicOr(reinterpret_cast<unsigned *>(&S.dmask[lr & ~1]), (1u << k) << (16 * (lr & 1)));
+            continue;
+        }
+        if (fl & 1) f8_store_chunk(a, r, k, th);
+        if (k == 14) m[3] = v[3] = 0.f;       // the padding slot
+        __stcs(pm, f8_enc4_rn(m, &S.s_inv[0][4 * k]));
+        __stcs(pv, f8_enc4_sr(v, &S.s_inv[1][4 * k], f8_rnd(a, r, k)));
+    }
+    __syncthreads();
+    if (tid < 2 * kF8Cols) {                  // grow only
+        const int w = tid / kF8Cols, c = tid - w * kF8Cols;
+        const uint32_t b = S.s_max[w][c];
+        const float so = S.s_old[w][c];
+        if (b) {
+            const float s = fmaxf(so, pow2f(min(f8_scale_exp(b) + (so > 0.f ? 1 : 0), 126)));
+            if (s != so) {
+                S.s_inv[w][c] = __frcp_rn(s);
+                (w ? a.vsc : a.msc)[tile * 64 + c] = s;
+                S.mov[atomicAdd(&S.moved, 1)] = (uint8_t)(w << 6 | c);
+            }
+        }
+    }
+    __syncthreads();
+    // the chunks not listed, re-encoded in the columns whose scale grew
+    const int nmov = S.moved;
+    for (int idx = tid; idx < nrow * nmov; idx += kThreads) {
+        const int lr = idx / nmov, q = S.mov[idx - lr * nmov], w = q >> 6, c = q & 63;
+        if ((S.dmask[lr] >> (c >> 2)) & 1u) continue;
+        uint8_t *pb = (w ? gv : gm) + (r0 + lr) * kF8Row + c;
+        const float x = f8_dec(*pb) * S.s_old[w][c] * S.s_inv[w][c];
+        *pb = (uint8_t)(w ? f8_rn_floor(x) : f8_rn(x));
+    }
+    // pass 2: the listed chunks from their stored moments, under the grown scales
+    const int nd = S.nd;
+    for (int d = tid; d < nd; d += kThreads) {
+        const int j = S.dlist[d] >> 4, k = S.dlist[d] & 15;
+        const int lr = S.clist[j], fl = S.flg[lr];
+        const int64_t r = r0 + lr;
+        float th[4], g[4], m[4], v[4];
+        if (fl & 1) f8_load_chunk(a, r, k, th, g);
+        uint32_t *pm = reinterpret_cast<uint32_t *>(gm + r * kF8Row) + k;
+        uint32_t *pv = reinterpret_cast<uint32_t *>(gv + r * kF8Row) + k;
+        f8_dec4(*pm, &S.s_old[0][4 * k], m);
+        f8_dec4(*pv, &S.s_old[1][4 * k], v);
+        f8_apply_chunk(a, k, fl & 1, fl & 2, S.fac[lr], th, g, m, v);
+        if (fl & 1) f8_store_chunk(a, r, k, th);
+        if (k == 14) m[3] = v[3] = 0.f;
+        __stcs(pm, f8_enc4_rn(m, &S.s_inv[0][4 * k]));
+        __stcs(pv, f8_enc4_sr(v, &S.s_inv[1][4 * k], f8_rnd(a, r, k)));
+    }
+    if (tid < nrow && vis) reinterpret_cast<uint32_t *>(gm + row * kF8Row)[kF8TWord] = t_old + 1u;   // Sec. 3.2
+}
+
+// Shared arrays of a block on its full pass.
+struct F8FullShared {
+    uint32_t cm[kF8Tile * kF8Row / 4], cv[kF8Tile * kF8Row / 4];
+    __align__(16) float s_old[2][64], s_inv[2][64];
+    float s_new[2][64];
+    uint32_t s_max[2][64];
+    uint32_t s_wmax[kThreads / 32][2][kF8Row / 4 - 1];
+    uint8_t flg[kF8Tile];                     // bit 0 visible, bit 1 StSS-sampled
+    int16_t clist[kF8Tile];                   // rows that change (visible or sampled)
+    float2 fac[kF8Tile];
+    int s_nv, s_nc, s_moved;                  // s_moved: slots whose scale changed, listed in s_mov
+    uint8_t s_mov[2 * 64];                    // moment << 6 | slot
+};
+
+// The block one wave of resident CTAs ahead of `tile`: its means (or mask
+// bytes) asked of L2, as the other formats' steps do.
+__device__ __forceinline__ void f8_prefetch_ahead(const StepArgs &a, const int vis_src, const int tile)
+{
+    if (threadIdx.x != 0 || a.tile_ahead <= 0) return;
+    const int64_t q = ((int64_t)tile + a.tile_ahead) * kF8Tile;
+    if (q + kF8Tile > (int64_t)a.n_rows) return;
+    if (vis_src == kVisCamera && ((uintptr_t)a.a_xyz & 15u) == 0)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.a_xyz + q * 3), "n"(kF8Tile * 12) : "memory");
+    else if (vis_src == kVisMask && ((uintptr_t)a.mask_in & 15u) == 0)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.mask_in + q), "n"(kF8Tile) : "memory");
+}
+
+// A block on its full pass: its scales recomputed from every row.
+__device__ __forceinline__ void f8_block_full(const StepArgs &a, const int vis_src, const int tile, F8FullShared &F)
 {
     constexpr int kWords = kF8Row / 4 - 1;    // code words of a row (the last holds t)
     constexpr int kWarps = kThreads / 32;
-    __shared__ uint32_t cm[kF8Tile * kF8Row / 4], cv[kF8Tile * kF8Row / 4];
-    __shared__ __align__(16) float s_old[2][64], s_inv[2][64];
-    __shared__ float s_new[2][64];
-    __shared__ uint32_t s_max[2][64];
-    __shared__ uint32_t s_wmax[kWarps][2][kWords];
-    __shared__ uint8_t flg[kF8Tile];          // bit 0 visible, bit 1 StSS-sampled
-    __shared__ int16_t clist[kF8Tile];        // rows that change (visible or sampled)
-    __shared__ float2 fac[kF8Tile];
-    __shared__ int s_nv, s_nc, s_moved;       // s_moved: slots whose scale changed, listed in s_mov
-    __shared__ uint8_t s_mov[2 * 64];         // moment << 6 | slot
+    auto &cm = F.cm;
+    auto &cv = F.cv;
+    auto &s_old = F.s_old;
+    auto &s_inv = F.s_inv;
+    auto &s_new = F.s_new;
+    auto &s_max = F.s_max;
+    auto &s_wmax = F.s_wmax;
+    auto &flg = F.flg;
+    auto &clist = F.clist;
+    auto &fac = F.fac;
+    int &s_nv = F.s_nv, &s_nc = F.s_nc, &s_moved = F.s_moved;
+    auto &s_mov = F.s_mov;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t r0 = (int64_t)blockIdx.x * kF8Tile;
+    const int64_t r0 = (int64_t)tile * kF8Tile;
     const int nrow = (int)min((int64_t)kF8Tile, (int64_t)a.n_rows - r0);
-    prefetch_tile_ahead<kF8Tile>(a, vis_src);
 
     const uint4 *gm = reinterpret_cast<const uint4 *>(static_cast<const char *>(a.m) + r0 * kF8Row);
     const uint4 *gv = reinterpret_cast<const uint4 *>(static_cast<const char *>(a.v) + r0 * kF8Row);
@@ -229,8 +421,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) step_fp8(const StepArgs 
         reinterpret_cast<uint4 *>(cv)[q] = __ldcs(gv + q);
     }
     if (tid < 64) {
-        s_old[0][tid] = tid < kF8Cols ? a.msc[blockIdx.x * 64 + tid] : 0.f;
-        s_old[1][tid] = tid < kF8Cols ? a.vsc[blockIdx.x * 64 + tid] : 0.f;
+        s_old[0][tid] = tid < kF8Cols ? a.msc[tile * 64 + tid] : 0.f;
+        s_old[1][tid] = tid < kF8Cols ? a.vsc[tile * 64 + tid] : 0.f;
     }
     if (tid == 0) s_nv = s_nc = s_moved = 0;
 
@@ -336,7 +528,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) step_fp8(const StepArgs 
         s_new[w][c] = s;
         s_inv[w][c] = s > 0.f ? __frcp_rn(s) : 0.f;      // exact: s is a power of two
         if (s != so) {
-            (w ? a.vsc : a.msc)[blockIdx.x * 64 + c] = s;
+            (w ? a.vsc : a.msc)[tile * 64 + c] = s;
             s_mov[atomicAdd(&s_moved, 1)] = (uint8_t)(w << 6 | c);
         }
     } else if (tid < 2 * kF8Cols + 2) {
@@ -384,6 +576,29 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) step_fp8(const StepArgs 
         __stcs(om4 + q, reinterpret_cast<const uint4 *>(cm)[q]);
         __stcs(ov4 + q, reinterpret_cast<const uint4 *>(cv)[q]);
     }
+}
+
+// One launch per step: the first n_full CTAs take the blocks on their full
+// pass (tile = full0 + kF8FullEvery * i), so that these longer CTAs start
+// first; every other CTA takes tile blockIdx.x - n_full on its grow-only
+// step (returning at once for the full-pass tiles).
+template <int kMinBlocks>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) step_fp8(const StepArgs a, const int vis_src, const int full0,
+                                                                  const int n_full)
+{
+    __shared__ union {
+        F8FullShared full;
+        F8GrowShared grow;
+    } sh;
+    if ((int)blockIdx.x < n_full) {
+        f8_block_full(a, vis_src, full0 + (int)kF8FullEvery * (int)blockIdx.x, sh.full);
+        return;
+    }
+    const int tile = (int)blockIdx.x - n_full;
+    if ((uint32_t)tile % kF8FullEvery == (uint32_t)full0) return;
+    f8_prefetch_ahead(a, vis_src, tile);
+    const int nrow = (int)min((int64_t)kF8Tile, (int64_t)a.n_rows - (int64_t)tile * kF8Tile);
+    f8_block_grow(a, vis_src, tile, nrow, sh.grow);
 }
 
 // ------------------------------------------------------ export / import
@@ -522,8 +737,11 @@ cudaError_t launch_step_fp8(const StepArgs &a, int vis_src, cudaStream_t s)
     static int s_res[64] = {};
     StepArgs b = a;
     b.tile_ahead = resident_ctas(reinterpret_cast<const void *>(k), s_res);
-    const unsigned grid = (unsigned)((a.n_rows + kF8Tile - 1) / kF8Tile);
-    k<<<grid, kThreads, 0, s>>>(b, vis_src);
+    const int n_tiles = (int)((a.n_rows + kF8Tile - 1) / kF8Tile);
+    // the tiles of this step's full pass: (iteration + tile) % kF8FullEvery == 0
+    const int full0 = (int)((kF8FullEvery - (uint32_t)(a.k_ctr % kF8FullEvery)) % kF8FullEvery);
+    const int n_full = full0 < n_tiles ? (n_tiles - full0 + (int)kF8FullEvery - 1) / (int)kF8FullEvery : 0;
+    k<<<(unsigned)(n_full + n_tiles), kThreads, 0, s>>>(b, vis_src, full0, n_full);
     return cudaGetLastError();
 }
 

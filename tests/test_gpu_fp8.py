@@ -4,7 +4,9 @@ Bounds, from the arithmetic.  The step computes every moment in FP32 and
 only the stored copy is rounded, so after one step from zero state the
 attributes equal the FP32 path's bit for bit, and every block scale s is the
 smallest power of two with amax / s <= 448 (from zero state a scale only
-grows to fit; later steps shrink it only by two binades or more).  A stored
+grows to fit; later steps grow it to twice the smallest fitting one, and a
+block's full pass, one step in 128, shrinks it when that is two binades or
+more below).  A stored
 moment x is then within half an e4m3 ulp, 2^-4 |x|, where x / s is normal
 (>= 2^-6), and within half the subnormal spacing, 2^-10 s, below; the second
 moment, rounded stochastically, within one ulp (2^-3 |x| or 2^-9 s); a
@@ -182,4 +184,49 @@ def test_unsupported_combinations(G):
     # the context stays usable
     run.step_mask(None, G.make_params(LR, 1))
     assert G.gs_opt_sync_errors(run.h) == G.GS_OK
+    run.close()
+
+
+def test_scale_growth_reencodes_the_other_rows(G):
+    """A step where a block's scales may only grow (iteration 5: neither of
+    the two blocks takes its full pass, which comes when iteration + block
+    is a multiple of 128).  One visible row of block 0 takes a gradient far
+    above the imported moments, so the first-moment scales of its columns
+    must grow to twice the smallest power of two that fits the new values;
+    the block's other rows keep their values, re-encoded under the grown
+    scale (to nearest; a positive second moment never to zero), and block 1
+    keeps its codes and scales."""
+    n = 512
+    run = GpuScene(synth.scene_uniform(n, 980), prec=G.GS_MOM_FP8E4M3)
+    rng = np.random.default_rng(981)
+    m = (rng.normal(size=(n, 59)) * 1e-3).astype(np.float32)
+    v = (rng.random((n, 59)) * 1e-6 + 1e-8).astype(np.float32)
+    G.gs_opt_import_state(run.h, torch.from_numpy(m).cuda(), torch.from_numpy(v).cuda(), None)
+    m0, v0, _ = run.state()
+    grads = np.zeros((n, 59), np.float32)
+    grads[7] = 50.0                            # (1 - beta1) * 50 = 5: far outside 448 * scale(1e-3)
+    run.set_grads(grads)
+    mask = np.zeros(n, np.uint8)
+    mask[7] = 1
+    run.step_mask(torch.from_numpy(mask).cuda(), G.make_params(LR, 5))
+    m1, v1, t1 = run.state()
+    assert t1[7] == 1 and np.all(np.delete(t1, 7) == 0)
+    # the changed row: m = 0.1 * (50 - m0) + m0 rounded once more under the grown scale
+    m_new = np.float32(0.1) * (np.float32(50.0) - m0[7]) + m0[7]
+    e_fit = np.ceil(np.log2(np.abs(m_new).astype(np.float64) / 448.0))
+    s_new = np.ldexp(1.0, (e_fit + 1).astype(np.int64))          # one binade of headroom
+    assert np.all(np.abs(m1[7] - m_new) <= 2.0 ** -4 * np.abs(m_new) + 2.0 ** -10 * s_new)
+    # the other rows of block 0, column by column, under the grown scales
+    kept = np.r_[0:7, 8:256]
+    q = _e4m3((m0[kept].astype(np.float64) / s_new).astype(np.float32))
+    assert m1[kept].tobytes() == (q.astype(np.float64) * s_new).astype(np.float32).tobytes()
+    # v of the changed row is (1 - beta2) * 2500 = 2.5: its scales grow too; the kept rows'
+    # second moments fall below the smallest subnormal there and keep it (never zero)
+    v_new = np.float32(1e-3) * (np.float32(2500.0) - v0[7]) + v0[7]
+    sv_new = np.ldexp(1.0, (np.ceil(np.log2(np.abs(v_new).astype(np.float64) / 448.0)) + 1).astype(np.int64))
+    qv = _e4m3((v0[kept].astype(np.float64) / sv_new).astype(np.float32))
+    qv = np.where((qv == 0) & (v0[kept] > 0), np.float32(2.0 ** -9), qv)
+    assert v1[kept].tobytes() == (qv.astype(np.float64) * sv_new).astype(np.float32).tobytes()
+    # block 1 untouched
+    assert m1[256:].tobytes() == m0[256:].tobytes() and v1[256:].tobytes() == v0[256:].tobytes()
     run.close()
