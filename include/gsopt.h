@@ -78,17 +78,21 @@ typedef enum gs_moment_prec {
                                iteration, row, slot)                              */
     GS_MOM_FP8E4M3 = 2,     /* all 59 columns e4m3 (64 B per moment and row, t in
                                the m row) with one FP32 scale per column and block
-                               of 256 rows, a power of two: each step it grows at
-                               once to keep the block's largest magnitude within
-                               e4m3's 448, and shrinks only when it can drop by two
-                               binades or more (import sets the smallest that
-                               fits).  A scale change re-encodes that column in all
-                               256 rows.  m rounded to nearest, v stochastically (+-1/2
+                               of 256 rows, a power of two that keeps the block's
+                               magnitudes within e4m3's 448.  On most steps a scale
+                               only grows, when the changed rows' values need it (to
+                               twice the smallest fitting power of two once it is
+                               set); on one step in 128 per block (iteration + block
+                               a multiple of 128) it is recomputed from all 256 rows
+                               and shrinks when it can drop by two binades or more
+                               (import sets the smallest that fits).  A scale change
+                               re-encodes that column in the block's other rows.
+                               m rounded to nearest, v stochastically (+-1/2
                                e4m3 ulp dither, then nearest); a positive v is never
                                stored as zero.  3 mantissa bits: far outside a 1e-3
                                error budget (measured by the tests and the bench).
-                               Not with the extended step's terms (noise, AIU,
-                               active count) or in a batch: GS_ERR_UNSUPPORTED.  */
+                               Not with the optional terms (noise, AIU, active
+                               count) or in a batch: GS_ERR_UNSUPPORTED.  */
     GS_MOM_BF16_HYBRID = 3, /* the 45 SH-rest columns BF16 (m round-to-nearest, v
                                stochastically rounded from a counter hash of (seed,
                                iteration, row, slot)); the other 14 columns FP32  */
