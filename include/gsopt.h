@@ -81,11 +81,12 @@ typedef enum gs_moment_prec {
                                of 256 rows, a power of two that keeps the block's
                                magnitudes within e4m3's 448.  On most steps a scale
                                only grows, when the changed rows' values need it (to
-                               twice the smallest fitting power of two once it is
+                               8 x the smallest fitting power of two once it is
                                set); on one step in 128 per block (iteration + block
                                a multiple of 128) it is recomputed from all 256 rows
-                               and shrinks when it can drop by two binades or more
-                               (import sets the smallest that fits).  A scale change
+                               and shrinks, to 8 x the smallest fitting, when that
+                               is more than 3 binades below (import sets the
+                               smallest that fits).  A scale change
                                re-encodes that column in the block's other rows.
                                m rounded to nearest, v stochastically (+-1/2
                                e4m3 ulp dither, then nearest); a positive v is never

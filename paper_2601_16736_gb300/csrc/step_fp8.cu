@@ -14,11 +14,12 @@
 //   * on most steps the scales may only grow (f8_block_grow): only the rows
 //     that change are read and written, straight from and to device memory,
 //     and a column whose new values no longer fit takes a larger power of
-//     two, with the block's other rows re-encoded in that column alone;
+//     two (kF8Headroom binades above the smallest fitting one), with the
+//     block's other rows re-encoded in that column alone;
 //   * on one step in kF8FullEvery (staggered over the blocks: iteration +
 //     block a multiple of it) the block's full pass recomputes every scale
 //     from all 256 rows, staged in shared memory, and shrinks it when the
-//     smallest fitting power of two is two binades or more below it:
+//     smallest fitting power of two is more than kF8Headroom binades below:
 //       0. the largest code magnitude per column over the rows that stay as
 //          they are (a bytewise integer max: e4m3 magnitudes order as their
 //          codes);
@@ -47,6 +48,12 @@ constexpr int kF8MinBlocks = 4;
 // on one step in kF8FullEvery, staggered over the blocks; on the others
 // they may only grow.
 constexpr uint32_t kF8FullEvery = 128;
+// Binades above the smallest fitting power of two that a scale takes when it
+// moves (except from zero): a block's moments rise over many steps while v
+// builds up, and each move re-encodes the column in the block's other rows.
+// 0, 1, 2, 3 and 4 binades gave the same 1000-step error on the 3 M
+// workload; 3 was the fastest.
+constexpr int kF8Headroom = 3;
 static_assert(kF8Tile == kThreads, "one row per thread in phase A");
 
 __device__ __forceinline__ float f8_dec(uint32_t code)
@@ -233,10 +240,10 @@ struct F8GrowShared {
 // memory, in one pass: a chunk whose new moments fit the range of the
 // current scales (448 s) is stored at once; a chunk with a value outside it
 // is left as it was and listed.  A column with such a value then takes the
-// smallest power of two that fits it (twice that when the column already
-// had a scale, so that a moment still rising does not move it again on the
-// next steps; the full pass keeps a scale up to two binades above the
-// smallest fitting), the block's other chunks are re-encoded in that column,
+// smallest power of two that fits it (kF8Headroom binades above that when
+// the column already had a scale, so that a moment still rising does not
+// move it again on the next steps), the block's other chunks are
+// re-encoded in that column,
 // byte by byte in place (a changed row's new value is then rounded twice),
 // and the listed chunks are updated from their stored moments and encoded
 // under the grown scales.
@@ -327,7 +334,7 @@ __device__ __forceinline__ void f8_block_grow(const StepArgs &a, const int vis_s
         const uint32_t b = S.s_max[w][c];
         const float so = S.s_old[w][c];
         if (b) {
-            const float s = fmaxf(so, pow2f(min(f8_scale_exp(b) + (so > 0.f ? 1 : 0), 126)));
+            const float s = fmaxf(so, pow2f(min(f8_scale_exp(b) + (so > 0.f ? kF8Headroom : 0), 126)));
             if (s != so) {
                 S.s_inv[w][c] = __frcp_rn(s);
                 (w ? a.vsc : a.msc)[tile * 64 + c] = s;
@@ -512,10 +519,12 @@ __device__ __forceinline__ void f8_block_full(const StepArgs &a, const int vis_s
     }
     __syncthreads();
     if (tid < 2 * kF8Cols) {
-        // the new scale: grows at once to fit the slot's largest magnitude;
-        // shrinks only when it could drop by two binades or more (a scale
-        // change re-encodes the slot in all 256 rows; one binade of slack
-        // costs at most one bit at the bottom of e4m3's range)
+        // the new scale: grows at once when the slot's largest magnitude no
+        // longer fits, shrinks when the smallest fitting power of two is more
+        // than kF8Headroom binades below; a move (except from zero) lands
+        // kF8Headroom binades above the smallest fitting one (a scale change
+        // re-encodes the slot in all 256 rows; each binade of slack costs at
+        // most one bit at the bottom of e4m3's range)
         const int w = tid / kF8Cols, c = tid - w * kF8Cols;
         const uint32_t b = s_max[w][c];
         const float so = s_old[w][c];
@@ -523,7 +532,8 @@ __device__ __forceinline__ void f8_block_full(const StepArgs &a, const int vis_s
         if (b) {
             const int e = f8_scale_exp(b);
             const int eo = so > 0.f ? (int)(__float_as_uint(so) >> 23) - 127 : -1000;
-            if (e > eo || e <= eo - 2) s = pow2f(e);
+            if (e > eo) s = pow2f(so > 0.f ? min(e + kF8Headroom, 126) : e);
+            else if (e <= eo - kF8Headroom - 1) s = pow2f(min(e + kF8Headroom, 126));
         }
         s_new[w][c] = s;
         s_inv[w][c] = s > 0.f ? __frcp_rn(s) : 0.f;      // exact: s is a power of two

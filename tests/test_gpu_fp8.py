@@ -4,9 +4,9 @@ Bounds, from the arithmetic.  The step computes every moment in FP32 and
 only the stored copy is rounded, so after one step from zero state the
 attributes equal the FP32 path's bit for bit, and every block scale s is the
 smallest power of two with amax / s <= 448 (from zero state a scale only
-grows to fit; later steps grow it to twice the smallest fitting one, and a
-block's full pass, one step in 128, shrinks it when that is two binades or
-more below).  A stored
+grows to fit; later steps grow it to 8 x the smallest fitting one, and a
+block's full pass, one step in 128, shrinks it to that when the smallest
+fitting one is more than 3 binades below).  A stored
 moment x is then within half an e4m3 ulp, 2^-4 |x|, where x / s is normal
 (>= 2^-6), and within half the subnormal spacing, 2^-10 s, below; the second
 moment, rounded stochastically, within one ulp (2^-3 |x| or 2^-9 s); a
@@ -192,7 +192,7 @@ def test_scale_growth_reencodes_the_other_rows(G):
     the two blocks takes its full pass, which comes when iteration + block
     is a multiple of 128).  One visible row of block 0 takes a gradient far
     above the imported moments, so the first-moment scales of its columns
-    must grow to twice the smallest power of two that fits the new values;
+    must grow to 8 x the smallest power of two that fits the new values;
     the block's other rows keep their values, re-encoded under the grown
     scale (to nearest; a positive second moment never to zero), and block 1
     keeps its codes and scales."""
@@ -214,7 +214,7 @@ def test_scale_growth_reencodes_the_other_rows(G):
     # the changed row: m = 0.1 * (50 - m0) + m0 rounded once more under the grown scale
     m_new = np.float32(0.1) * (np.float32(50.0) - m0[7]) + m0[7]
     e_fit = np.ceil(np.log2(np.abs(m_new).astype(np.float64) / 448.0))
-    s_new = np.ldexp(1.0, (e_fit + 1).astype(np.int64))          # one binade of headroom
+    s_new = np.ldexp(1.0, (e_fit + 3).astype(np.int64))          # three binades of headroom
     assert np.all(np.abs(m1[7] - m_new) <= 2.0 ** -4 * np.abs(m_new) + 2.0 ** -10 * s_new)
     # the other rows of block 0, column by column, under the grown scales
     kept = np.r_[0:7, 8:256]
@@ -223,7 +223,7 @@ def test_scale_growth_reencodes_the_other_rows(G):
     # v of the changed row is (1 - beta2) * 2500 = 2.5: its scales grow too; the kept rows'
     # second moments fall below the smallest subnormal there and keep it (never zero)
     v_new = np.float32(1e-3) * (np.float32(2500.0) - v0[7]) + v0[7]
-    sv_new = np.ldexp(1.0, (np.ceil(np.log2(np.abs(v_new).astype(np.float64) / 448.0)) + 1).astype(np.int64))
+    sv_new = np.ldexp(1.0, (np.ceil(np.log2(np.abs(v_new).astype(np.float64) / 448.0)) + 3).astype(np.int64))
     qv = _e4m3((v0[kept].astype(np.float64) / sv_new).astype(np.float32))
     qv = np.where((qv == 0) & (v0[kept] > 0), np.float32(2.0 ** -9), qv)
     assert v1[kept].tobytes() == (qv.astype(np.float64) * sv_new).astype(np.float32).tobytes()
