@@ -318,7 +318,8 @@ inline cudaError_t launch_pdl(void (*kernel)(Args...), unsigned grid, unsigned b
 // (defined in the kernel translation units, called by api.cu)
 
 cudaError_t launch_step(const StepArgs &a, int prec, int vis_src, cudaStream_t s);
-// the step with position noise, AIU or the active count (launch_step forwards to it)
+// the step with AIU or noise on every row (launch_step forwards to it; the count
+// and noise on visible rows alone take the plain kernel's terms form)
 cudaError_t launch_step_ext(const StepArgs &a, int prec, int vis_src, cudaStream_t s);
 // Batched launch with candidate configuration `cand` (0 .. batch_candidates-1)
 // over the device scene table p (tile_start built for that candidate's tile
