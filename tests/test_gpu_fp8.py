@@ -108,9 +108,11 @@ def test_first_step_equals_fp32_path(G):
 
 @pytest.mark.parametrize("n", [1, 255, 256, 257, 513])
 def test_edge_sizes_follow_fp32_path(G, orc, n):
-    """Four masked steps: t and the visibility follow the oracle exactly; the
-    attributes differ from the FP32 path's by at most half of the summed
-    per-step movement (moment rounding of a few e4m3 ulps fed back)."""
+    """Five masked steps (the last, iteration 128, is block 0's full pass;
+    the others are grow-only steps): t and the visibility follow the oracle
+    exactly; the attributes differ from the FP32 path's by at most half of
+    the summed per-step movement (moment rounding of a few e4m3 ulps fed
+    back)."""
     groups = synth.scene_uniform(n, 950 + n)
     rng = np.random.default_rng(n)
     r32 = GpuScene(groups, prec=G.GS_MOM_FP32)
@@ -118,7 +120,7 @@ def test_edge_sizes_follow_fp32_path(G, orc, n):
     ref = OracleRun(orc, synth.to_rows(groups))
     moved = np.zeros((n, 59))
     prev = r32.rows().astype(np.float64)
-    for k in (1, 2, 3, 100):
+    for k in (1, 2, 3, 100, 128):
         grads = synth.grads_rows(n, 951, k)
         mask_np = (rng.random(n) < 0.6).astype(np.uint8)
         p = G.make_params(LR, k, restate=(k == 100), restate_ratio=0.5, seed=3)
