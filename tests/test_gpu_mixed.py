@@ -199,14 +199,15 @@ def _run_sampled(G, orc, wl, prec, sample):
 
 
 # (format, meets the 1e-3 gate, regression bound on the largest group error)
-MIXED_3M = [("FP16_BLOCK", True, 1e-3), ("BF16_HYBRID", True, 1e-3), ("BF16", False, 3e-2),
+MIXED_3M = [("FP32", True, 1e-4), ("FP16_BLOCK", True, 1e-3), ("BF16_HYBRID", True, 1e-3), ("BF16", False, 3e-2),
             ("FP8E4M3", False, 0.1)]
 
 
 @pytest.mark.parametrize("prec,meets_gate,bound", MIXED_3M)
 def test_3m_1000_steps_sampled(G, orc, prec, meets_gate, bound):
     """The 3 M-primitive, 1000-step workload (about 20 % visible per view),
-    followed by the oracle on 2000 sampled primitives.  The formats that
+    followed by the oracle on 2000 sampled primitives.  FP32 moments are held
+    to the FP32 parity bound after 1000 steps (1e-4); the formats that
     meet the 1e-3 gate are asserted against it; the others are held to a
     recorded regression bound and then marked as failing the gate (xfail,
     with the measured error), which is not a pass."""
