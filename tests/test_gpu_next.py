@@ -118,6 +118,42 @@ def test_noise_matches_oracle(G, orc, prec, mode):
     run.close()
 
 
+@pytest.mark.parametrize("prec", ["FP32", "FP16_BLOCK"])
+@pytest.mark.parametrize("n", [1, 255, 257, 513, 1537])
+def test_terms_form_edge_sizes(G, orc, prec, n):
+    """The terms form (active count and noise on visible rows, RSR on one
+    step) at sizes around the 256-row tiles, with all-visible, none-visible
+    and random masks: rows against the oracle, the count against the
+    classification of the GPU's own logits, step counters exact."""
+    groups = _noisy_scene(n, 1960 + n)
+    run = GpuScene(groups, prec=getattr(G, "GS_MOM_" + prec))
+    st = orc.State(synth.to_rows(groups))
+    cfg = orc.Config(n_i=orc.dar_normaliser(800 * 800))
+    rng = np.random.default_rng(1961 + n)
+    na = torch.zeros(1, dtype=torch.int64, device="cuda")
+    masks = [np.ones(n, np.uint8), np.zeros(n, np.uint8)] + [(rng.random(n) < 0.4).astype(np.uint8) for _ in range(4)]
+    for k, mask in enumerate(masks, start=1):
+        g = synth.grads_rows(n, 1962 + n, k)
+        lr = synth.lr_for_step(k, len(masks))
+        o, ext = _ext(G, orc, noise=1, noise_lr=400.0, noise_k=3.0, noise_t=0.5)
+        ext.seed = 78
+        rs = k == 3
+        run.set_grads(g)
+        na.zero_()
+        run.step_mask(torch.from_numpy(mask).cuda(),
+                      G.make_params(lr, k, restate=rs, restate_ratio=0.5, seed=78, n_active=na, **o))
+        orc.step_ext(cfg, st, g, mask, lr, True, True, k, ext)
+        if rs:
+            orc.restate(cfg, st, 78, k, 0.5)
+        got_tau = run.attrs["opacity"].cpu().numpy().ravel()
+        assert int(na.item()) == orc.active_rows(got_tau).size
+    tol = 1e-5 if prec == "FP32" else 2e-3
+    assert_close(run.rows(), st.theta, tol, what=f"terms form, {n} rows")
+    _, _, t = run.state()
+    assert np.array_equal(t, st.t)
+    run.close()
+
+
 def test_noise_only_rows_move_by_the_noise_term(G, orc):
     """First step, g = 0, DAR off: the Adam direction is 0 and the position
     change is exactly the noise term (visible and, in mode 2, invisible)."""
