@@ -66,6 +66,14 @@ def bytes_visible(prec: str) -> int:
     return 3 * 236 + STATE_RW[prec] + T_RW[prec] - 12
 
 
+def launch_bytes(prec: str, n_rows: int, n_visible: int, rsr_rows: int) -> int:
+    """Algorithmic bytes of one fused step launch: every row's mean for the
+    frustum test, each visible row's attributes, gradients, moments and step
+    counter (its mean already counted), and the moments of each invisible
+    StSS-sampled row that RSR scales."""
+    return n_visible * bytes_visible(prec) + n_rows * BYTES_ROW_VIS + rsr_rows * STATE_RW[prec]
+
+
 def _peaks():
     p = ROOT / "MEASURED_PEAKS.json"
     if p.exists():
@@ -282,12 +290,12 @@ def timed_run(G, sc, prec, steps, warmup, clocks_device=None, dist=None, extra=N
         if k % sc.wl.restate_every == 0:
             rsr_steps.append(k)
             rsr += int(round(sc.wl.restate_ratio * (sc.wl.n - int(nv[warmup + j]))))
-    byt = (timed_nv * bytes_visible(prec) + steps * sc.wl.n * BYTES_ROW_VIS + rsr * STATE_RW[prec]) / steps
+    byt = launch_bytes(prec, steps * sc.wl.n, timed_nv, rsr) / steps
     # the first timed launch: the one an ncu capture skipping the warm-up launches (-s warmup -c 1) takes
     k1, nv1 = sc.k(warmup), int(nv[warmup])
     rsr1 = int(round(sc.wl.restate_ratio * (sc.wl.n - nv1))) if k1 % sc.wl.restate_every == 0 else 0
     first = dict(iteration=k1, visible_rows=nv1, rsr_rows=rsr1,
-                 algorithmic_bytes=nv1 * bytes_visible(prec) + sc.wl.n * BYTES_ROW_VIS + rsr1 * STATE_RW[prec])
+                 algorithmic_bytes=launch_bytes(prec, sc.wl.n, nv1, rsr1))
     out = dict(elapsed=elapsed, step_s=elapsed / steps, nv=timed_nv, bytes_per_launch=byt, clocks=clocks,
                steps=steps, rsr_steps=rsr_steps, rsr_rows=rsr, first_timed=first)
     if instrument:

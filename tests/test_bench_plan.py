@@ -46,3 +46,19 @@ def test_camera_order_index_wraps(bench):
     # Scene.cam(i) indexes order[(k - 1) % len(order)]; k goes past len(order) here
     assert all(0 <= (k0 + i) % len(order) < len(order) for i in range(25))
     assert len(order) >= 25
+
+
+def test_launch_bytes_per_row():
+    """Algorithmic bytes of a launch from the per-row counts: a visible FP32
+    row reads attributes, gradients, m, v (4 x 236 B) and writes attributes,
+    m, v (3 x 236 B), and reads and writes its 4-B step counter; its 12-B
+    mean is counted once, with every row's frustum test.  An invisible
+    StSS-sampled row has its m and v read and written."""
+    import bench
+    assert bench.launch_bytes("fp32", 1, 1, 0) == 7 * 236 + 8
+    assert bench.launch_bytes("fp32", 1_000_000, 0, 0) == 12_000_000
+    assert bench.launch_bytes("fp32", 10, 3, 2) == 3 * 1648 + 10 * 12 + 2 * 4 * 236
+    # FP16 block: 2 x 126 B of moments and a 2-B counter per moment row, read and written
+    assert bench.bytes_visible("fp16_block") == 3 * 236 + 4 * 126 + 4 - 12
+    assert bench.launch_bytes("fp16_block", 1_000_000, 268_093, 0) == 334_783_972
+    assert bench.launch_bytes("fp32", 1_000_000, 268_093, 0) == 453_817_264
