@@ -501,9 +501,9 @@ def run_ours(args):
                 legs[prec]["error"] = error_vs_fp32(G, msc, prec)
         for prec in ("fp16_block", "bf16_hybrid", "bf16", "fp8_e4m3"):
             legs[prec]["speedup_vs_fp32"] = legs[prec]["value"] / legs["fp32"]["value"]
-        legs["fp8_e4m3"]["bytes"] = ("algorithmic: 59 B per moment per visible row; the kernel also reads the "
-                                     "64-B code rows of every invisible row (its block's scale depends on them) and "
-                                     "rewrites a block's rows when a column scale moves")
+        legs["fp8_e4m3"]["bytes"] = ("algorithmic: 59 B per moment per visible row; the kernel also re-encodes a "
+                                     "block's other rows in a column whose scale grows, and reads every row's codes "
+                                     "on the block's full pass (one step in 128)")
         out["mixed_precision"] = {"workload": f"{mwl.name}: {mwl.n} Gaussians, ~20% visible, {args.mixed_steps} "
                                               f"timed steps per format", "gate": "group relative L2 vs the FP32 step <= 1e-3",
                                   **legs}
